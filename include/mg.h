@@ -1,0 +1,145 @@
+/*
+ * mg.h - C ABI of the GB300 nested-grid Poisson / 2LPT / displacement library.
+ *
+ * The library solves  L phi = f  (L = finite-difference Laplacian of order 2, 4
+ * or 6, Table 1 of Hahn & Abel 2011, arXiv:1103.6031) on a periodic base grid
+ * with a chain of nested refinement patches (refinement factor 2, Sec. 3.3) by
+ * FAS multigrid V-cycles (Sec. 3.2), computes the second-order LPT source
+ * tau = sum_{i<j}(phi_,ii phi_,jj - phi_,ij^2) (Sec. 3.1.2) and the displacement
+ * field psi = -grad phi (Sec. 3.1.1).  Every step runs in CUDA kernels on one GPU.
+ *
+ * Conventions
+ *   - Arrays are float64, dense, row-major [nx][ny][nz] (z fastest), one array
+ *     per level; level 0 is the periodic base, level i >= 1 is nest i-1.
+ *   - A nest of size nest_n (even on every axis, in its own cells) covers the
+ *     parent cells [nest_off, nest_off + nest_n/2) on each axis.  Its region must
+ *     keep a margin of at least `order` parent cells to the parent's edges.
+ *   - Grid spacing h_0 = box / base_n[0]; h_i = h_{i-1} / 2.  The base must be
+ *     cubic in spacing (box applies to every axis, h is isotropic).
+ *   - phi solves L phi = f - <f>, where <f> is the volume-weighted mean over
+ *     leaf cells (cells not covered by a finer level); phi has zero mean over the
+ *     base level.  In covered cells the returned phi and f hold the average of
+ *     their 8 children.
+ *   - psi = -G phi (Table 1 gradient); the caller combines x = q + D1 psi1 +
+ *     (3/7) D1^2 psi2 (growth factors are the caller's).
+ *
+ * Ownership: inputs and outputs are caller-owned; device pointers unless a
+ * call says otherwise.  The hierarchy owns its padded working state, allocated
+ * through cfg->dev_alloc/dev_free (cudaMalloc/cudaFree when both are NULL) and
+ * released by mg_hierarchy_destroy.  Calls are ordered on the hierarchy's
+ * stream; the solve calls read one 16-byte convergence record back per V-cycle
+ * (so they return with the stream synchronised).
+ *
+ * Errors: every call returns an mg_status; no exception or abort crosses the
+ * ABI.  mg_last_error() gives a message for the last failing call on a handle.
+ */
+#ifndef MG_H
+#define MG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MG_MAX_LEVELS 16
+#define MG_MAX_HISTORY 64
+
+typedef struct mg_hierarchy mg_hierarchy;
+
+typedef enum {
+  MG_OK = 0,
+  MG_EINVAL = 1,   /* invalid configuration or argument                        */
+  MG_ENOMEM = 2,   /* the allocator returned NULL                              */
+  MG_ENOCONV = 3,  /* max_cycles reached above tol; outputs hold the last iterate */
+  MG_ECUDA = 4,    /* a CUDA runtime call or kernel launch failed              */
+  MG_ETIMEOUT = 5  /* reserved: bounded device-side wait expired               */
+} mg_status;
+
+typedef enum { MG_FP64 = 0, MG_MIXED = 1 } mg_precision;
+
+typedef struct {
+  int n_levels;                        /* 1 = base only; 1 + number of nests            */
+  int base_n[3];                       /* periodic base grid                            */
+  double box;                          /* base box length                               */
+  int nest_n[MG_MAX_LEVELS - 1][3];    /* nest i (level i+1): size in its own cells     */
+  int nest_off[MG_MAX_LEVELS - 1][3];  /* nest i: origin in parent cells                */
+  int order;                           /* FD order: 2, 4 or 6                           */
+  int precision;                       /* mg_precision                                  */
+  int nu1, nu2;                        /* pre/post smoothing sweeps (paper: 2, 2)       */
+  int max_cycles;                      /* V-cycle limit per solve                       */
+  double tol;                          /* stop when leaf |r| / leaf |f| <= tol          */
+  void* (*dev_alloc)(size_t bytes, void* ctx);
+  void (*dev_free)(void* ptr, void* ctx);
+  void* alloc_ctx;
+} mg_config;
+
+typedef struct {
+  int cycles;                          /* V-cycles run                                  */
+  double rel_residual;                 /* final leaf |r| / leaf |f|                     */
+  double source_mean;                  /* composite mean removed from the source        */
+  double history[MG_MAX_HISTORY];      /* rel_residual after each cycle                 */
+} mg_info;
+
+/* Fill *cfg with defaults: order 2, FP64, nu1 = nu2 = 2, max_cycles 50,
+ * tol 1e-10, box 1, no nests, NULL allocator.  Host only. */
+void mg_config_default(mg_config* cfg);
+
+/* Check the geometry and parameters without touching a GPU.  On failure
+ * returns MG_EINVAL and writes a message into msg (if msg != NULL, len > 0). */
+mg_status mg_config_validate(const mg_config* cfg, char* msg, size_t len);
+
+/* Device bytes the hierarchy for *cfg allocates (for admission by HBM budget);
+ * 0 if the configuration is invalid.  Host only. */
+size_t mg_workspace_bytes(const mg_config* cfg);
+
+/* Number of levels (full multigrid coarsenings below the base + base + nests)
+ * the V-cycle visits; 0 if invalid.  Host only. */
+int mg_total_levels(const mg_config* cfg);
+
+/* Create a hierarchy on the current CUDA device; cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream).  *out is NULL on failure. */
+mg_status mg_hierarchy_create(const mg_config* cfg, void* cuda_stream, mg_hierarchy** out);
+
+/* Free the working state (NULL-safe). */
+mg_status mg_hierarchy_destroy(mg_hierarchy* h);
+
+/* 1LPT potential (Sec. 3.1.1, 3.2-3.3): solve L phi = delta - <delta>.
+ * delta[l], phi[l]: n_levels device pointers, dense float64 per level.
+ * info may be NULL. */
+mg_status mg_solve_1lpt(mg_hierarchy* h, const double* const delta[], double* const phi[],
+                        mg_info* info);
+
+/* 2LPT potential (Sec. 3.1.2): tau(phi1) with FD second derivatives, then
+ * L phi2 = tau - <tau>.  phi1 as returned by mg_solve_1lpt. */
+mg_status mg_solve_2lpt(mg_hierarchy* h, const double* const phi1[], double* const phi2[],
+                        mg_info* info);
+
+/* Displacement psi = -G phi (Sec. 3.1.1, Table 1 gradient) on every level.
+ * disp[3*l + a] is component a (x, y, z) of level l, dense float64. */
+mg_status mg_displacements(mg_hierarchy* h, const double* const phi[], double* const disp[]);
+
+/* The 2LPT source tau on every level (before mean removal); covered cells hold
+ * the average of their children.  Same layout as delta. */
+mg_status mg_lpt2_source(mg_hierarchy* h, const double* const phi1[], double* const tau[]);
+
+/* One whole initial-conditions step: phi1 = solve(delta), phi2 = solve(tau(phi1)),
+ * disp1 = -G phi1, disp2 = -G phi2.  host_buffers != 0: every pointer is a host
+ * pointer and the call copies inputs in and outputs out on its stream (pinned
+ * host memory gives asynchronous copies); otherwise all are device pointers.
+ * Any output array pointer may be NULL to skip that output's copy-out. */
+mg_status mg_lpt_pipeline(mg_hierarchy* h, int host_buffers, const double* const delta[],
+                          double* const phi1[], double* const phi2[], double* const disp1[],
+                          double* const disp2[], mg_info* info1, mg_info* info2);
+
+/* Message for the last failing call on h ("" if none; NULL-safe). */
+const char* mg_last_error(const mg_hierarchy* h);
+
+/* Library version string. */
+const char* mg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MG_H */

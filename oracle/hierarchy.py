@@ -1,8 +1,9 @@
 """Levels, ghost zones and inter-level transfer for the composite (nested) grid.
 
 Level structure (Sec. 3.2-3.3, Fig. 3): levels 0..B-1 are the full periodic
-multigrid coarsenings of the base grid B (refinement factor 2, down to a side
-of at most 8 or an odd side); levels B+1.. are nested rectangular patches, each
+multigrid coarsenings of the base grid B (refinement factor 2; halving stops
+once some side is odd, no side exceeds 8, or a halved side would be narrower
+than the ghost width); levels B+1.. are nested rectangular patches, each
 inside its parent, at twice the parent's resolution.  Every level stores u
 with a ghost shell of width g = n/2 (n = order of the FD Laplacian).  Arrays
 are float64, [x][y][z], z fastest.
@@ -65,7 +66,11 @@ class Hierarchy:
         self.box = float(geom.box)
         base_n = tuple(geom.base_n)
         chain = [base_n]
-        while all(v % 2 == 0 for v in chain[-1]) and max(chain[-1]) > 8:
+        g = ghost_width(self.order)
+        # coarsen while every side is even, some side exceeds 8, and every side of the
+        # coarser level still holds a full ghost width
+        while (all(v % 2 == 0 for v in chain[-1]) and max(chain[-1]) > 8
+               and min(chain[-1]) // 2 >= g):
             chain.append(tuple(v // 2 for v in chain[-1]))
         chain.reverse()
         self.base = len(chain) - 1

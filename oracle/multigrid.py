@@ -108,7 +108,8 @@ def composite_mean(hier, fields):
     total = 0.0
     for l, fld in zip(hier.leaf_levels(), fields):
         total += hier.levels[l].h ** 3 * float(np.sum(fld[hier.uncovered_mask(l)]))
-    return total / np.prod([hier.box] * 3)
+    base = hier.levels[hier.base]
+    return total / (base.h ** 3 * np.prod(base.n))
 
 
 def prepare_source(hier, sources):

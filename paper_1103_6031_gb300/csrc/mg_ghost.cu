@@ -1,0 +1,323 @@
+// Ghost zones (Hahn & Abel 2011, Sec. 3.2 periodic boundaries; Sec. 3.3
+// coarse-fine boundaries).
+//
+// Coarse-fine faces of a nest, in three kernels:
+//  * k_cf_tangential (once per parent state): for each face, each of the n/2
+//    parent layers outside it and each fine tangential position, the degree-n
+//    tensor Lagrange interpolant of the parent values parallel to the face
+//    ("intermediate values"); and the part of the parent face flux (Table 2,
+//    order n-1) that reads uncovered parent cells.
+//  * k_cf_flux (before every half-sweep / residual): per parent face element,
+//    the ghosts of its 4 fine columns from a degree-n polynomial normal to the
+//    face through the n/2 intermediate values and n/2+1 fine interior values;
+//    the parent flux with covered parent cells taken as the mean of their
+//    current 8 children (two-way interface); the mean of the 4 fine fluxes;
+//    and the difference added uniformly to the ghosts of each column so that
+//    the fine fluxes average to the parent flux.
+//  * k_cf_edges (before the 2LPT source only): edge and corner ghosts, which
+//    only mixed derivatives read, by tensor degree-n interpolation of parent
+//    values.
+#include "mg_internal.h"
+
+namespace mgk {
+
+namespace {
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_ghost_periodic(Grid G, T* __restrict__ u) {
+  const long long g = G.g;
+  const long long X = G.n0 + 2 * g, Y = G.n1 + 2 * g;
+  const long long cntA = X * Y * 2 * g;
+  const long long cntB = X * 2 * g * G.n2;
+  const long long cntC = 2 * g * (long long)G.n1 * G.n2;
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  int i, j, k;
+  if (t < cntA) {
+    const int kk = (int)(t % (2 * g));
+    t /= 2 * g;
+    j = (int)(t % Y) - (int)g;
+    i = (int)(t / Y) - (int)g;
+    k = kk < g ? kk - (int)g : G.n2 + kk - (int)g;
+  } else if (t < cntA + cntB) {
+    t -= cntA;
+    k = (int)(t % G.n2);
+    t /= G.n2;
+    const int jj = (int)(t % (2 * g));
+    i = (int)(t / (2 * g)) - (int)g;
+    j = jj < g ? jj - (int)g : G.n1 + jj - (int)g;
+  } else if (t < cntA + cntB + cntC) {
+    t -= cntA + cntB;
+    k = (int)(t % G.n2);
+    t /= G.n2;
+    j = (int)(t % G.n1);
+    const int ii = (int)(t / G.n1);
+    i = ii < g ? ii - (int)g : G.n0 + ii - (int)g;
+  } else {
+    return;
+  }
+  const int si = ((i % G.n0) + G.n0) % G.n0;
+  const int sj = ((j % G.n1) + G.n1) % G.n1;
+  const int sk = ((k % G.n2) + G.n2) % G.n2;
+  u[gidx(G, i, j, k)] = u[gidx(G, si, sj, sk)];
+}
+
+__device__ __forceinline__ void face_axes(int a, int& b, int& c) {
+  b = (a == 0) ? 1 : 0;
+  c = (a == 2) ? 1 : 2;
+}
+
+__device__ __forceinline__ int face_of(const FaceSet& fs, long long t, const long long* base) {
+  int f = 0;
+#pragma unroll
+  for (int q = 1; q < 6; ++q)
+    if (t >= base[q]) f = q;
+  return f;
+}
+
+template <int ORDER, typename T>
+__global__ void __launch_bounds__(128)
+    k_cf_tangential(Grid F, Grid P, const T* __restrict__ pu, Int3 off, FaceSet fs, CfWeights w,
+                    T invH, T* __restrict__ inter, T* __restrict__ fc_unc) {
+  constexpr int half = ORDER / 2;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= fs.base[6]) return;
+  const int f = face_of(fs, t, fs.base);
+  const int a = f >> 1, side = f & 1;
+  int b, c;
+  face_axes(a, b, c);
+  const int nt0 = fs.nt[f][0], nt1 = fs.nt[f][1];
+  long long loc = t - fs.base[f];
+  const int m = (int)(loc / ((long long)nt0 * nt1));
+  loc -= (long long)m * nt0 * nt1;
+  const int tj = (int)(loc / nt1), tk = (int)(loc % nt1);
+  const int offs[3] = {off.x, off.y, off.z};
+  const int nf[3] = {F.n0, F.n1, F.n2};
+  const int pn = side == 0 ? offs[a] - 1 - m : offs[a] + nf[a] / 2 + m;
+  const int pb = offs[b] + (tj >> 1), pc = offs[c] + (tk >> 1);
+  const double* wb = w.tang[tj & 1];
+  const double* wc = w.tang[tk & 1];
+  T acc = T(0);
+  int crd[3];
+  crd[a] = pn;
+#pragma unroll
+  for (int bb = 0; bb <= ORDER; ++bb) {
+    crd[b] = pb + bb - half;
+    T row = T(0);
+#pragma unroll
+    for (int cc = 0; cc <= ORDER; ++cc) {
+      crd[c] = pc + cc - half;
+      row = fma(T(wc[cc]), __ldg(pu + gidx(P, crd[0], crd[1], crd[2])), row);
+    }
+    acc = fma(T(wb[bb]), row, acc);
+  }
+  inter[t] = acc;
+  if (m == 0 && ((tj | tk) & 1) == 0) {
+    // uncovered part of the parent face flux for element (tj/2, tk/2)
+    crd[b] = pb;
+    crd[c] = pc;
+    const int pface = side == 0 ? offs[a] : offs[a] + nf[a] / 2;
+    T fc = T(0);
+    const int s0 = side == 0 ? 0 : half, s1 = side == 0 ? half : ORDER;
+    for (int s = s0; s < s1; ++s) {
+      crd[a] = pface - half + s;
+      fc = fma(T(w.flux[s]), __ldg(pu + gidx(P, crd[0], crd[1], crd[2])), fc);
+    }
+    fc_unc[fs.ebase[f] + (long long)(tj >> 1) * (nt1 / 2) + (tk >> 1)] = fc * invH;
+  }
+}
+
+template <int ORDER, typename T>
+__global__ void __launch_bounds__(128)
+    k_cf_flux(Grid F, T* __restrict__ u, FaceSet fs, CfWeights w, const T* __restrict__ inter,
+              const T* __restrict__ fc_unc, T h, T invh, T invH, int flux_fix) {
+  constexpr int half = ORDER / 2;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= fs.ebase[6]) return;
+  const int f = face_of(fs, t, fs.ebase);
+  const int a = f >> 1, side = f & 1;
+  int b, c;
+  face_axes(a, b, c);
+  const int nt0 = fs.nt[f][0], nt1 = fs.nt[f][1];
+  const long long loc = t - fs.ebase[f];
+  const int jc = (int)(loc / (nt1 / 2)), kc = (int)(loc % (nt1 / 2));
+  const int nf[3] = {F.n0, F.n1, F.n2};
+  const int na = nf[a];
+  int crd[3];
+  // parent flux: uncovered part (precomputed) + covered cells as mean of 8 children
+  T fc = fc_unc[t];
+  {
+    T cov = T(0);
+#pragma unroll
+    for (int d = 0; d < half; ++d) {
+      const int s = side == 0 ? half + d : half - 1 - d;
+      const int i0 = side == 0 ? 2 * d : na - 2 - 2 * d;
+      T sum = T(0);
+#pragma unroll
+      for (int di = 0; di < 2; ++di)
+#pragma unroll
+        for (int dj = 0; dj < 2; ++dj)
+#pragma unroll
+          for (int dk = 0; dk < 2; ++dk) {
+            crd[a] = i0 + di;
+            crd[b] = 2 * jc + dj;
+            crd[c] = 2 * kc + dk;
+            sum += u[gidx(F, crd[0], crd[1], crd[2])];
+          }
+      cov = fma(T(w.flux[s]), sum * T(0.125), cov);
+    }
+    fc = fma(cov, invH, fc);
+  }
+  T ghost[4][half];
+  T ffsum = T(0);
+#pragma unroll
+  for (int col = 0; col < 4; ++col) {
+    const int tj = 2 * jc + (col >> 1), tk = 2 * kc + (col & 1);
+    crd[b] = tj;
+    crd[c] = tk;
+    T v[half + 1];
+#pragma unroll
+    for (int q = 0; q <= half; ++q) {
+      crd[a] = side == 0 ? q : na - 1 - q;
+      v[q] = u[gidx(F, crd[0], crd[1], crd[2])];
+    }
+    T cq[half];
+#pragma unroll
+    for (int q = 0; q < half; ++q)
+      cq[q] = inter[fs.base[f] + ((long long)q * nt0 + tj) * nt1 + tk];
+#pragma unroll
+    for (int m = 0; m < half; ++m) {
+      T gv = T(0);
+#pragma unroll
+      for (int q = 0; q < half; ++q) gv = fma(T(w.ncoarse[m][q]), cq[q], gv);
+#pragma unroll
+      for (int q = 0; q <= half; ++q) gv = fma(T(w.nfine[m][q]), v[q], gv);
+      ghost[col][m] = gv;
+    }
+    T ff = T(0);
+#pragma unroll
+    for (int s = 0; s < ORDER; ++s) {
+      T x;
+      if (side == 0) x = s < half ? ghost[col][half - 1 - s] : v[s - half];
+      else x = s < half ? v[half - 1 - s] : ghost[col][s - half];
+      ff = fma(T(w.flux[s]), x, ff);
+    }
+    ffsum += ff * invh;
+  }
+  T shift = T(0);
+  if (flux_fix) shift = (fc - T(0.25) * ffsum) * h / T(w.ghost_coef[side]);
+#pragma unroll
+  for (int col = 0; col < 4; ++col) {
+    crd[b] = 2 * jc + (col >> 1);
+    crd[c] = 2 * kc + (col & 1);
+#pragma unroll
+    for (int m = 0; m < half; ++m) {
+      crd[a] = side == 0 ? -1 - m : na + m;
+      u[gidx(F, crd[0], crd[1], crd[2])] = ghost[col][m] + shift;
+    }
+  }
+}
+
+template <int ORDER, typename T>
+__global__ void __launch_bounds__(128)
+    k_cf_edges(Grid F, T* __restrict__ u, Grid P, const T* __restrict__ pu, Int3 off,
+               CfWeights w) {
+  constexpr int half = ORDER / 2;
+  const int g = F.g;
+  const int X = F.n0 + 2 * g, Y = F.n1 + 2 * g, Z = F.n2 + 2 * g;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)X * Y * Z) return;
+  const int k = (int)(t % Z) - g;
+  const int j = (int)((t / Z) % Y) - g;
+  const int i = (int)(t / ((long long)Z * Y)) - g;
+  const int out = (i < 0 || i >= F.n0) + (j < 0 || j >= F.n1) + (k < 0 || k >= F.n2);
+  if (out < 2) return;
+  const int pi = off.x + (i >> 1), pj = off.y + (j >> 1), pk = off.z + (k >> 1);
+  const double* wi = w.tang[i & 1];
+  const double* wj = w.tang[j & 1];
+  const double* wk = w.tang[k & 1];
+  T acc = T(0);
+  for (int a = 0; a <= ORDER; ++a) {
+    T pa = T(0);
+    for (int bq = 0; bq <= ORDER; ++bq) {
+      T row = T(0);
+      for (int cq = 0; cq <= ORDER; ++cq)
+        row = fma(T(wk[cq]), __ldg(pu + gidx(P, pi + a - half, pj + bq - half, pk + cq - half)), row);
+      pa = fma(T(wj[bq]), row, pa);
+    }
+    acc = fma(T(wi[a]), pa, acc);
+  }
+  u[gidx(F, i, j, k)] = acc;
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_ghost_periodic(const Grid& G, T* u, cudaStream_t s) {
+  const long long g = G.g;
+  const long long X = G.n0 + 2 * g, Y = G.n1 + 2 * g;
+  const long long total = X * Y * 2 * g + X * 2 * g * G.n2 + 2 * g * (long long)G.n1 * G.n2;
+  const int block = 256;
+  k_ghost_periodic<T><<<(unsigned)((total + block - 1) / block), block, 0, s>>>(G, u);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cf_tangential(int order, const Grid& F, const Grid& P, const T* pu, Int3 off,
+                                 const FaceSet& fs, const CfWeights& w, double invH, T* inter,
+                                 T* fc_unc, cudaStream_t s) {
+  const int block = 128;
+  const unsigned grid = (unsigned)((fs.base[6] + block - 1) / block);
+  switch (order) {
+    case 2: k_cf_tangential<2, T><<<grid, block, 0, s>>>(F, P, pu, off, fs, w, T(invH), inter, fc_unc); break;
+    case 4: k_cf_tangential<4, T><<<grid, block, 0, s>>>(F, P, pu, off, fs, w, T(invH), inter, fc_unc); break;
+    case 6: k_cf_tangential<6, T><<<grid, block, 0, s>>>(F, P, pu, off, fs, w, T(invH), inter, fc_unc); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cf_flux(int order, const Grid& F, T* u, const FaceSet& fs, const CfWeights& w,
+                           const T* inter, const T* fc_unc, double h, double invh, double invH,
+                           int flux_fix, cudaStream_t s) {
+  const int block = 128;
+  const unsigned grid = (unsigned)((fs.ebase[6] + block - 1) / block);
+  switch (order) {
+    case 2: k_cf_flux<2, T><<<grid, block, 0, s>>>(F, u, fs, w, inter, fc_unc, T(h), T(invh), T(invH), flux_fix); break;
+    case 4: k_cf_flux<4, T><<<grid, block, 0, s>>>(F, u, fs, w, inter, fc_unc, T(h), T(invh), T(invH), flux_fix); break;
+    case 6: k_cf_flux<6, T><<<grid, block, 0, s>>>(F, u, fs, w, inter, fc_unc, T(h), T(invh), T(invH), flux_fix); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cf_edges(int order, const Grid& F, T* u, const Grid& P, const T* pu, Int3 off,
+                            const CfWeights& w, cudaStream_t s) {
+  const long long total = (long long)(F.n0 + 2 * F.g) * (F.n1 + 2 * F.g) * (F.n2 + 2 * F.g);
+  const int block = 128;
+  const unsigned grid = (unsigned)((total + block - 1) / block);
+  switch (order) {
+    case 2: k_cf_edges<2, T><<<grid, block, 0, s>>>(F, u, P, pu, off, w); break;
+    case 4: k_cf_edges<4, T><<<grid, block, 0, s>>>(F, u, P, pu, off, w); break;
+    case 6: k_cf_edges<6, T><<<grid, block, 0, s>>>(F, u, P, pu, off, w); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+#define MGK_GHOST_INSTANTIATE(T)                                                              \
+  template cudaError_t launch_ghost_periodic<T>(const Grid&, T*, cudaStream_t);               \
+  template cudaError_t launch_cf_tangential<T>(int, const Grid&, const Grid&, const T*, Int3, \
+                                               const FaceSet&, const CfWeights&, double, T*,  \
+                                               T*, cudaStream_t);                             \
+  template cudaError_t launch_cf_flux<T>(int, const Grid&, T*, const FaceSet&,                \
+                                         const CfWeights&, const T*, const T*, double,        \
+                                         double, double, int, cudaStream_t);                  \
+  template cudaError_t launch_cf_edges<T>(int, const Grid&, T*, const Grid&, const T*, Int3,  \
+                                          const CfWeights&, cudaStream_t);
+
+MGK_GHOST_INSTANTIATE(double)
+MGK_GHOST_INSTANTIATE(float)
+
+}  // namespace mgk

@@ -1,0 +1,116 @@
+// Internal declarations shared by the CUDA translation units of the library.
+//
+// Device layout of one level: the interior n0 x n1 x n2 cells plus a ghost
+// shell of width g = order/2 on every side, row-major [x][y][z] with z fastest.
+// Along z the interior starts at element za = 4 (>= g) and rows are padded to
+// a pitch Zp that is a multiple of 8 elements, so every interior row starts on
+// a 32-byte boundary and even z indices allow 16-byte vector access for
+// float64 (and 16-byte access for groups of 4 at z = 0 mod 4 for float32).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mgk {
+
+struct Grid {
+  int n0, n1, n2;  // interior extent
+  int g;           // ghost width
+  int za;          // z index of the first interior element within a row
+  int Y;           // padded extent along y (n1 + 2g)
+  int Zp;          // row pitch in elements
+  int X;           // padded extent along x (n0 + 2g)
+};
+
+__host__ __device__ inline long long gidx(const Grid& G, int i, int j, int k) {
+  return ((long long)(i + G.g) * G.Y + (j + G.g)) * G.Zp + (k + G.za);
+}
+
+inline long long grid_elems(const Grid& G) { return (long long)G.X * G.Y * G.Zp; }
+
+Grid make_grid(int n0, int n1, int n2, int g);
+
+struct Int3 {
+  int x, y, z;
+};
+
+// Interpolation weights for the coarse-fine ghost zones, computed on the host
+// from their Lagrange definition (see mg_weights.cpp).
+struct CfWeights {
+  double tang[2][7];   // [fine parity][parent offset -half..half]
+  double ncoarse[3][3];  // [ghost layer m][coarse node q]
+  double nfine[3][4];    // [ghost layer m][fine node q]
+  double flux[6];        // face-flux weights on cells face-half .. face+half-1
+  double ghost_coef[2];  // sum of flux weights on the ghost side: [low face, high face]
+};
+
+void compute_cf_weights(int order, CfWeights* w);
+
+// Geometry of the 6 faces of a nest for the face kernels.
+struct FaceSet {
+  int nt[6][2];         // tangential extents (fine cells) of face f: axes b, c
+  long long base[7];    // prefix sums of half * nt0 * nt1 (intermediate values per face)
+  long long ebase[7];   // prefix sums of (nt0/2) * (nt1/2) (parent face elements per face)
+};
+
+void make_faceset(const Grid& F, int half, FaceSet* fs);
+
+// ---- kernels: smoothing and inter-level transfer (mg_smooth.cu) ----
+template <typename T>
+cudaError_t launch_smooth_half(int order, const Grid& G, const T* uin, T* uout, const T* f,
+                               double a_f, int colour, cudaStream_t s);
+template <typename T>
+cudaError_t launch_residual_restrict(int order, const Grid& F, const T* u, const T* f,
+                                     double invh2, const Grid& P, T* pu, T* pfas, T* ubar,
+                                     Int3 off, Int3 cn, cudaStream_t s);
+template <typename T>
+cudaError_t launch_fas_source(int order, const Grid& P, const T* pu, T* pfas, double invH2,
+                              Int3 off, Int3 cn, cudaStream_t s);
+template <typename T>
+cudaError_t launch_prolong(const Grid& F, T* u, const Grid& P, const T* pu, const T* ubar,
+                           Int3 off, Int3 cn, cudaStream_t s);
+template <typename T>
+cudaError_t launch_restrict_u(const Grid& F, const T* u, const Grid& P, T* pu, Int3 off,
+                              Int3 cn, cudaStream_t s);
+
+// ---- kernels: ghost zones (mg_ghost.cu) ----
+template <typename T>
+cudaError_t launch_ghost_periodic(const Grid& G, T* u, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cf_tangential(int order, const Grid& F, const Grid& P, const T* pu, Int3 off,
+                                 const FaceSet& fs, const CfWeights& w, double invH, T* inter,
+                                 T* fc_unc, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cf_flux(int order, const Grid& F, T* u, const FaceSet& fs, const CfWeights& w,
+                           const T* inter, const T* fc_unc, double h, double invh, double invH,
+                           int flux_fix, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cf_edges(int order, const Grid& F, T* u, const Grid& P, const T* pu, Int3 off,
+                            const CfWeights& w, cudaStream_t s);
+
+// ---- kernels: coarsest solve, norms, packing, 2LPT, gradient (mg_misc.cu) ----
+cudaError_t launch_coarsest(const Grid& G, const double* f, double* u, const double* kern,
+                            cudaStream_t s);
+// partial sums over uncovered interior cells of level G: [2*b] = sum r^2, [2*b+1] = sum f^2
+// (times vol), r = f - L u; blocks = number of partial slots written.
+cudaError_t launch_norm_partial(int order, const Grid& G, const double* u, const double* f,
+                                double invh2, double vol, Int3 clo, Int3 chi, double* partial,
+                                int blocks, cudaStream_t s);
+cudaError_t launch_sum_partial(const Grid& G, const double* f, double vol, Int3 clo, Int3 chi,
+                               double* partial, int blocks, cudaStream_t s);
+cudaError_t launch_reduce_partials(const double* partial, int count, int width, double* out,
+                                   cudaStream_t s);
+cudaError_t launch_pack(const Grid& G, const double* src, double* dst, double shift,
+                        cudaStream_t s);
+cudaError_t launch_unpack(const Grid& G, const double* src, double* dst, cudaStream_t s);
+cudaError_t launch_shift_copy(const Grid& G, double* f, double* f2, const double* mean_num,
+                              double inv_volume, cudaStream_t s);
+cudaError_t launch_fill(double* p, long long n, double v, cudaStream_t s);
+cudaError_t launch_lpt2_source(int order, const Grid& G, const double* phi, double invh2,
+                               double* tau, cudaStream_t s);
+cudaError_t launch_gradient(int order, const Grid& G, const double* phi, double invh, double* dx,
+                            double* dy, double* dz, cudaStream_t s);
+
+int norm_blocks(const Grid& G);
+
+}  // namespace mgk

@@ -1,0 +1,344 @@
+// Coarsest-level solve, convergence norms, composite mean, packing between the
+// caller's dense arrays and the padded level layout, the 2LPT source and the
+// displacement gradient (Hahn & Abel 2011, Sec. 3.1, 3.2).
+#include "mg_internal.h"
+#include "mg_stencil.cuh"
+
+namespace mgk {
+
+namespace {
+
+// Table 1 gradient: antisymmetric weights on offsets +1, +2, +3 (units 1/h).
+template <int ORDER>
+struct Grad;
+template <>
+struct Grad<2> {
+  static constexpr double g1 = 0.5, g2 = 0.0, g3 = 0.0;
+};
+template <>
+struct Grad<4> {
+  static constexpr double g1 = 8.0 / 12.0, g2 = -1.0 / 12.0, g3 = 0.0;
+};
+template <>
+struct Grad<6> {
+  static constexpr double g1 = 45.0 / 60.0, g2 = -9.0 / 60.0, g3 = 1.0 / 60.0;
+};
+
+template <int ORDER>
+__device__ __forceinline__ double grad_w(int s) {  // weight at offset s in [-3, 3]
+  const int a = s < 0 ? -s : s;
+  const double v = a == 1 ? Grad<ORDER>::g1 : (a == 2 ? Grad<ORDER>::g2 : (a == 3 ? Grad<ORDER>::g3 : 0.0));
+  return s < 0 ? -v : v;
+}
+
+template <int ORDER>
+__device__ __forceinline__ double lap_w(int s) {
+  const int a = s < 0 ? -s : s;
+  return a == 0 ? Lap<ORDER>::w0 : (a == 1 ? Lap<ORDER>::w1 : (a == 2 ? Lap<ORDER>::w2 : Lap<ORDER>::w3));
+}
+
+// Periodic pseudo-inverse of L on the coarsest level as a circular convolution:
+// u(x) = sum_y K(x - y) f(y), K precomputed on the host from the DFT symbol.
+__global__ void __launch_bounds__(128)
+    k_coarsest(Grid G, const double* __restrict__ f, double* __restrict__ u,
+               const double* __restrict__ kern) {
+  const int n = G.n0 * G.n1 * G.n2;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= n) return;
+  const int xk = x % G.n2, xj = (x / G.n2) % G.n1, xi = x / (G.n1 * G.n2);
+  double acc = 0.0;
+  for (int yi = 0; yi < G.n0; ++yi) {
+    const int di = (xi - yi + G.n0) % G.n0;
+    for (int yj = 0; yj < G.n1; ++yj) {
+      const int dj = (xj - yj + G.n1) % G.n1;
+      const double* krow = kern + ((long long)di * G.n1 + dj) * G.n2;
+      const double* frow = f + gidx(G, yi, yj, 0);
+      for (int yk = 0; yk < G.n2; ++yk) {
+        const int dk = (xk - yk + G.n2) % G.n2;
+        acc = fma(__ldg(krow + dk), __ldg(frow + yk), acc);
+      }
+    }
+  }
+  u[gidx(G, xi, xj, xk)] = acc;
+}
+
+template <int BLOCK>
+__device__ __forceinline__ void block_sum2(double& a, double& b) {
+  __shared__ double sa[BLOCK], sb[BLOCK];
+  sa[threadIdx.x] = a;
+  sb[threadIdx.x] = b;
+  __syncthreads();
+#pragma unroll
+  for (int w = BLOCK / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      sa[threadIdx.x] += sa[threadIdx.x + w];
+      sb[threadIdx.x] += sb[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  a = sa[0];
+  b = sb[0];
+}
+
+constexpr int kRedBlock = 256;
+
+__device__ __forceinline__ bool covered(int i, int j, int k, Int3 lo, Int3 hi) {
+  return i >= lo.x && i < hi.x && j >= lo.y && j < hi.y && k >= lo.z && k < hi.z;
+}
+
+template <int ORDER>
+__global__ void __launch_bounds__(kRedBlock)
+    k_norm_partial(Grid G, const double* __restrict__ u, const double* __restrict__ f,
+                   double invh2, double vol, Int3 clo, Int3 chi, double* __restrict__ partial) {
+  const long long n = (long long)G.n0 * G.n1 * G.n2;
+  const long long sy = G.Zp, sx = (long long)G.Y * G.Zp;
+  double rr = 0.0, ff = 0.0;
+  for (long long t = blockIdx.x * (long long)kRedBlock + threadIdx.x; t < n;
+       t += (long long)gridDim.x * kRedBlock) {
+    const int k = (int)(t % G.n2), j = (int)((t / G.n2) % G.n1), i = (int)(t / ((long long)G.n2 * G.n1));
+    if (covered(i, j, k, clo, chi)) continue;
+    const long long p = gidx(G, i, j, k);
+    const double fv = __ldg(f + p);
+    const double r = fma(-invh2, lap_h2<ORDER, double>(u, p, sy, sx), fv);
+    rr = fma(r, r, rr);
+    ff = fma(fv, fv, ff);
+  }
+  block_sum2<kRedBlock>(rr, ff);
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = rr * vol;
+    partial[2 * blockIdx.x + 1] = ff * vol;
+  }
+}
+
+__global__ void __launch_bounds__(kRedBlock)
+    k_sum_partial(Grid G, const double* __restrict__ f, double vol, Int3 clo, Int3 chi,
+                  double* __restrict__ partial) {
+  const long long n = (long long)G.n0 * G.n1 * G.n2;
+  double s = 0.0, unused = 0.0;
+  for (long long t = blockIdx.x * (long long)kRedBlock + threadIdx.x; t < n;
+       t += (long long)gridDim.x * kRedBlock) {
+    const int k = (int)(t % G.n2), j = (int)((t / G.n2) % G.n1), i = (int)(t / ((long long)G.n2 * G.n1));
+    if (covered(i, j, k, clo, chi)) continue;
+    s += __ldg(f + gidx(G, i, j, k));
+  }
+  block_sum2<kRedBlock>(s, unused);
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = s * vol;
+    partial[2 * blockIdx.x + 1] = 0.0;
+  }
+}
+
+// Sums `count` consecutive (a, b) pairs in a fixed order into out[0], out[1].
+__global__ void __launch_bounds__(kRedBlock)
+    k_reduce_partials(const double* __restrict__ partial, int count, double* __restrict__ out) {
+  double a = 0.0, b = 0.0;
+  for (int t = threadIdx.x; t < count; t += kRedBlock) {
+    a += partial[2 * t];
+    b += partial[2 * t + 1];
+  }
+  block_sum2<kRedBlock>(a, b);
+  if (threadIdx.x == 0) {
+    out[0] = a;
+    out[1] = b;
+  }
+}
+
+__global__ void __launch_bounds__(256)
+    k_pack(Grid G, const double* __restrict__ src, double* __restrict__ dst, double shift) {
+  const long long n = (long long)G.n0 * G.n1 * G.n2;
+  const long long t = blockIdx.x * 256LL + threadIdx.x;
+  if (t >= n) return;
+  const int k = (int)(t % G.n2), j = (int)((t / G.n2) % G.n1), i = (int)(t / ((long long)G.n2 * G.n1));
+  dst[gidx(G, i, j, k)] = __ldg(src + t) - shift;
+}
+
+__global__ void __launch_bounds__(256)
+    k_unpack(Grid G, const double* __restrict__ src, double* __restrict__ dst) {
+  const long long n = (long long)G.n0 * G.n1 * G.n2;
+  const long long t = blockIdx.x * 256LL + threadIdx.x;
+  if (t >= n) return;
+  const int k = (int)(t % G.n2), j = (int)((t / G.n2) % G.n1), i = (int)(t / ((long long)G.n2 * G.n1));
+  dst[t] = __ldg(src + gidx(G, i, j, k));
+}
+
+// f -= mean, f2 = f on the interior; mean = *mean_num * inv_volume (device-side).
+__global__ void __launch_bounds__(256)
+    k_shift_copy(Grid G, double* __restrict__ f, double* __restrict__ f2,
+                 const double* __restrict__ mean_num, double inv_volume) {
+  const long long n = (long long)G.n0 * G.n1 * G.n2;
+  const long long t = blockIdx.x * 256LL + threadIdx.x;
+  if (t >= n) return;
+  const int k = (int)(t % G.n2), j = (int)((t / G.n2) % G.n1), i = (int)(t / ((long long)G.n2 * G.n1));
+  const long long p = gidx(G, i, j, k);
+  const double v = f[p] - mean_num[0] * inv_volume;
+  f[p] = v;
+  f2[p] = v;
+}
+
+__global__ void __launch_bounds__(256) k_fill(double* __restrict__ p, long long n, double v) {
+  const long long t = blockIdx.x * 256LL + threadIdx.x;
+  if (t < n) p[t] = v;
+}
+
+// tau = sum_{i<j} (phi_ii phi_jj - phi_ij^2); phi_ii: 1D second difference,
+// phi_ij: composition of the 1D gradients along i and j (reads edge ghosts).
+template <int ORDER>
+__global__ void __launch_bounds__(128)
+    k_lpt2_source(Grid G, const double* __restrict__ phi, double invh2, double* __restrict__ tau) {
+  constexpr int half = ORDER / 2;
+  const long long n = (long long)G.n0 * G.n1 * G.n2;
+  const long long t = blockIdx.x * 128LL + threadIdx.x;
+  if (t >= n) return;
+  const int k = (int)(t % G.n2), j = (int)((t / G.n2) % G.n1), i = (int)(t / ((long long)G.n2 * G.n1));
+  const long long p = gidx(G, i, j, k);
+  const long long st[3] = {(long long)G.Y * G.Zp, (long long)G.Zp, 1};
+  double d[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double acc = 0.0;
+#pragma unroll
+    for (int s = -half; s <= half; ++s) acc = fma(lap_w<ORDER>(s), __ldg(phi + p + s * st[a]), acc);
+    d[a] = acc * invh2;
+  }
+  double m[3];
+  const int pa[3] = {0, 0, 1}, pb[3] = {1, 2, 2};
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    double acc = 0.0;
+#pragma unroll
+    for (int sa = -half; sa <= half; ++sa) {
+      if (sa == 0) continue;
+      double inner = 0.0;
+#pragma unroll
+      for (int sb = -half; sb <= half; ++sb) {
+        if (sb == 0) continue;
+        inner = fma(grad_w<ORDER>(sb), __ldg(phi + p + sa * st[pa[q]] + sb * st[pb[q]]), inner);
+      }
+      acc = fma(grad_w<ORDER>(sa), inner, acc);
+    }
+    m[q] = acc * invh2;
+  }
+  tau[p] = d[0] * d[1] + d[0] * d[2] + d[1] * d[2] - m[0] * m[0] - m[1] * m[1] - m[2] * m[2];
+}
+
+template <int ORDER>
+__global__ void __launch_bounds__(128)
+    k_gradient(Grid G, const double* __restrict__ phi, double invh, double* __restrict__ dx,
+               double* __restrict__ dy, double* __restrict__ dz) {
+  constexpr int half = ORDER / 2;
+  const long long n = (long long)G.n0 * G.n1 * G.n2;
+  const long long t = blockIdx.x * 128LL + threadIdx.x;
+  if (t >= n) return;
+  const int k = (int)(t % G.n2), j = (int)((t / G.n2) % G.n1), i = (int)(t / ((long long)G.n2 * G.n1));
+  const long long p = gidx(G, i, j, k);
+  const long long st[3] = {(long long)G.Y * G.Zp, (long long)G.Zp, 1};
+  double out[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double acc = 0.0;
+#pragma unroll
+    for (int s = 1; s <= half; ++s)
+      acc = fma(grad_w<ORDER>(s), __ldg(phi + p + s * st[a]) - __ldg(phi + p - s * st[a]), acc);
+    out[a] = -acc * invh;
+  }
+  dx[t] = out[0];
+  dy[t] = out[1];
+  dz[t] = out[2];
+}
+
+inline unsigned blocks_for(long long n, int b) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace
+
+int norm_blocks(const Grid& G) {
+  const long long n = (long long)G.n0 * G.n1 * G.n2;
+  long long b = (n + kRedBlock - 1) / kRedBlock;
+  if (b > 1216) b = 1216;  // 8 x 152 SMs
+  return (int)b;
+}
+
+cudaError_t launch_coarsest(const Grid& G, const double* f, double* u, const double* kern,
+                            cudaStream_t s) {
+  const int n = G.n0 * G.n1 * G.n2;
+  k_coarsest<<<blocks_for(n, 128), 128, 0, s>>>(G, f, u, kern);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_norm_partial(int order, const Grid& G, const double* u, const double* f,
+                                double invh2, double vol, Int3 clo, Int3 chi, double* partial,
+                                int blocks, cudaStream_t s) {
+  switch (order) {
+    case 2: k_norm_partial<2><<<blocks, kRedBlock, 0, s>>>(G, u, f, invh2, vol, clo, chi, partial); break;
+    case 4: k_norm_partial<4><<<blocks, kRedBlock, 0, s>>>(G, u, f, invh2, vol, clo, chi, partial); break;
+    case 6: k_norm_partial<6><<<blocks, kRedBlock, 0, s>>>(G, u, f, invh2, vol, clo, chi, partial); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum_partial(const Grid& G, const double* f, double vol, Int3 clo, Int3 chi,
+                               double* partial, int blocks, cudaStream_t s) {
+  k_sum_partial<<<blocks, kRedBlock, 0, s>>>(G, f, vol, clo, chi, partial);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_partials(const double* partial, int count, int width, double* out,
+                                   cudaStream_t s) {
+  (void)width;
+  k_reduce_partials<<<1, kRedBlock, 0, s>>>(partial, count, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const Grid& G, const double* src, double* dst, double shift,
+                        cudaStream_t s) {
+  const long long n = (long long)G.n0 * G.n1 * G.n2;
+  k_pack<<<blocks_for(n, 256), 256, 0, s>>>(G, src, dst, shift);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const Grid& G, const double* src, double* dst, cudaStream_t s) {
+  const long long n = (long long)G.n0 * G.n1 * G.n2;
+  k_unpack<<<blocks_for(n, 256), 256, 0, s>>>(G, src, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shift_copy(const Grid& G, double* f, double* f2, const double* mean_num,
+                              double inv_volume, cudaStream_t s) {
+  const long long n = (long long)G.n0 * G.n1 * G.n2;
+  k_shift_copy<<<blocks_for(n, 256), 256, 0, s>>>(G, f, f2, mean_num, inv_volume);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill(double* p, long long n, double v, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_fill<<<blocks_for(n, 256), 256, 0, s>>>(p, n, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lpt2_source(int order, const Grid& G, const double* phi, double invh2,
+                               double* tau, cudaStream_t s) {
+  const long long n = (long long)G.n0 * G.n1 * G.n2;
+  const unsigned b = blocks_for(n, 128);
+  switch (order) {
+    case 2: k_lpt2_source<2><<<b, 128, 0, s>>>(G, phi, invh2, tau); break;
+    case 4: k_lpt2_source<4><<<b, 128, 0, s>>>(G, phi, invh2, tau); break;
+    case 6: k_lpt2_source<6><<<b, 128, 0, s>>>(G, phi, invh2, tau); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gradient(int order, const Grid& G, const double* phi, double invh, double* dx,
+                            double* dy, double* dz, cudaStream_t s) {
+  const long long n = (long long)G.n0 * G.n1 * G.n2;
+  const unsigned b = blocks_for(n, 128);
+  switch (order) {
+    case 2: k_gradient<2><<<b, 128, 0, s>>>(G, phi, invh, dx, dy, dz); break;
+    case 4: k_gradient<4><<<b, 128, 0, s>>>(G, phi, invh, dx, dy, dz); break;
+    case 6: k_gradient<6><<<b, 128, 0, s>>>(G, phi, invh, dx, dy, dz); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace mgk

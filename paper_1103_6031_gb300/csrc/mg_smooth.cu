@@ -1,0 +1,239 @@
+// Red-black Gauss-Seidel half-sweeps, residual + restriction, FAS source and
+// prolongation-correction (Hahn & Abel 2011, Sec. 3.2 steps 2-9; Sec. 3.3).
+//
+// Smoother: one colour c = (i+j+k) mod 2 per launch.  Every cell of colour c
+// takes the value that solves its own row of L u = f with all other values
+// fixed at their pre-half-sweep values ("colour-Jacobi"; exact red-black GS for
+// the 7-point stencil; for 13/19 points same-colour cells at distance 2 couple
+// and this fixes their order).  The kernel reads buffer `uin` and writes every
+// interior cell of `uout` (colour c updated, the other colour copied), so no
+// thread ever reads a value another thread of the same launch writes.
+#include "mg_internal.h"
+#include "mg_stencil.cuh"
+
+namespace mgk {
+
+namespace {
+
+constexpr int kPairX = 32;  // z-pairs per block row
+constexpr int kRowsY = 4;   // y rows per block
+
+template <int ORDER, typename T>
+__global__ void __launch_bounds__(kPairX* kRowsY)
+    k_smooth_half(Grid G, const T* __restrict__ uin, T* __restrict__ uout,
+                  const T* __restrict__ f, T a_f, int colour) {
+  const int t = blockIdx.x * kPairX + threadIdx.x;
+  const int j = blockIdx.y * kRowsY + threadIdx.y;
+  const int i = blockIdx.z;
+  const int k0 = 2 * t;
+  if (j >= G.n1 || k0 >= G.n2) return;
+  const long long sy = G.Zp;
+  const long long sx = (long long)G.Y * G.Zp;
+  const long long p0 = gidx(G, i, j, k0);
+  const int upd = (((i + j + k0) & 1) == colour) ? 0 : 1;
+  const bool pair = (k0 + 1) < G.n2;
+  if (!pair && upd == 1) {
+    uout[p0] = __ldg(uin + p0);
+    return;
+  }
+  const long long p = p0 + upd;
+  T s1, s2, s3;
+  neighbour_sums<ORDER, T>(uin, p, sy, sx, s1, s2, s3);
+  // u = (h^2 f - sum_off w u_nb) / w_centre
+  constexpr double wc = 3.0 * Lap<ORDER>::w0;
+  T v = a_f * __ldg(f + p);
+  v = fma(T(-Lap<ORDER>::w1 / wc), s1, v);
+  if (ORDER >= 4) v = fma(T(-Lap<ORDER>::w2 / wc), s2, v);
+  if (ORDER >= 6) v = fma(T(-Lap<ORDER>::w3 / wc), s3, v);
+  if (pair) {
+    typedef typename Vec2<T>::type V2;
+    V2 out;
+    if (upd == 0) {
+      out.x = v;
+      out.y = __ldg(uin + p0 + 1);
+    } else {
+      out.x = __ldg(uin + p0);
+      out.y = v;
+    }
+    *reinterpret_cast<V2*>(uout + p0) = out;
+  } else {
+    uout[p0] = v;
+  }
+}
+
+// One thread per covered parent cell: r = f - L u at its 8 children,
+// parent u := mean(u), ubar := mean(u), parent f_fas := mean(r) (L ubar added later).
+template <int ORDER, typename T>
+__global__ void __launch_bounds__(128)
+    k_residual_restrict(Grid F, const T* __restrict__ u, const T* __restrict__ f, T invh2, Grid P,
+                        T* __restrict__ pu, T* __restrict__ pfas, T* __restrict__ ubar, Int3 off,
+                        Int3 cn) {
+  const int kc = blockIdx.x * blockDim.x + threadIdx.x;
+  const int jc = blockIdx.y * blockDim.y + threadIdx.y;
+  const int ic = blockIdx.z;
+  if (kc >= cn.z || jc >= cn.y) return;
+  const long long sy = F.Zp;
+  const long long sx = (long long)F.Y * F.Zp;
+  T su = T(0), sr = T(0);
+#pragma unroll
+  for (int di = 0; di < 2; ++di) {
+#pragma unroll
+    for (int dj = 0; dj < 2; ++dj) {
+#pragma unroll
+      for (int dk = 0; dk < 2; ++dk) {
+        const long long p = gidx(F, 2 * ic + di, 2 * jc + dj, 2 * kc + dk);
+        const T lu = lap_h2<ORDER, T>(u, p, sy, sx);
+        su += __ldg(u + p);
+        sr += fma(-invh2, lu, __ldg(f + p));
+      }
+    }
+  }
+  const long long q = gidx(P, off.x + ic, off.y + jc, off.z + kc);
+  const T mu = su * T(0.125);
+  pu[q] = mu;
+  pfas[q] = sr * T(0.125);
+  ubar[((long long)ic * cn.y + jc) * cn.z + kc] = mu;
+}
+
+// Covered parent cells: f_fas += L u (u = restricted fine solution there).
+template <int ORDER, typename T>
+__global__ void __launch_bounds__(128)
+    k_fas_source(Grid P, const T* __restrict__ pu, T* __restrict__ pfas, T invH2, Int3 off,
+                 Int3 cn) {
+  const int kc = blockIdx.x * blockDim.x + threadIdx.x;
+  const int jc = blockIdx.y * blockDim.y + threadIdx.y;
+  const int ic = blockIdx.z;
+  if (kc >= cn.z || jc >= cn.y) return;
+  const long long sy = P.Zp;
+  const long long sx = (long long)P.Y * P.Zp;
+  const long long q = gidx(P, off.x + ic, off.y + jc, off.z + kc);
+  pfas[q] = fma(invH2, lap_h2<ORDER, T>(pu, q, sy, sx), pfas[q]);
+}
+
+// u += inject(parent u - ubar) on the fine interior; one thread per z-pair.
+template <typename T>
+__global__ void __launch_bounds__(128)
+    k_prolong(Grid F, T* __restrict__ u, Grid P, const T* __restrict__ pu,
+              const T* __restrict__ ubar, Int3 off, Int3 cn) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int i = blockIdx.z;
+  const int k0 = 2 * t;
+  if (j >= F.n1 || k0 >= F.n2) return;
+  const int ic = i >> 1, jc = j >> 1, kc = t;
+  const T d = __ldg(pu + gidx(P, off.x + ic, off.y + jc, off.z + kc)) -
+              __ldg(ubar + ((long long)ic * cn.y + jc) * cn.z + kc);
+  const long long p = gidx(F, i, j, k0);
+  typedef typename Vec2<T>::type V2;
+  V2 v = *reinterpret_cast<const V2*>(u + p);
+  v.x += d;
+  v.y += d;
+  *reinterpret_cast<V2*>(u + p) = v;
+}
+
+// parent u := mean of children (covered region), one thread per parent cell.
+template <typename T>
+__global__ void __launch_bounds__(128)
+    k_restrict_u(Grid F, const T* __restrict__ u, Grid P, T* __restrict__ pu, Int3 off, Int3 cn) {
+  const int kc = blockIdx.x * blockDim.x + threadIdx.x;
+  const int jc = blockIdx.y * blockDim.y + threadIdx.y;
+  const int ic = blockIdx.z;
+  if (kc >= cn.z || jc >= cn.y) return;
+  T s = T(0);
+#pragma unroll
+  for (int di = 0; di < 2; ++di)
+#pragma unroll
+    for (int dj = 0; dj < 2; ++dj) {
+      typedef typename Vec2<T>::type V2;
+      const V2 v = *reinterpret_cast<const V2*>(u + gidx(F, 2 * ic + di, 2 * jc + dj, 2 * kc));
+      s += v.x + v.y;
+    }
+  pu[gidx(P, off.x + ic, off.y + jc, off.z + kc)] = s * T(0.125);
+}
+
+dim3 coarse_grid(Int3 cn, dim3 block) {
+  return dim3((cn.z + block.x - 1) / block.x, (cn.y + block.y - 1) / block.y, cn.x);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_smooth_half(int order, const Grid& G, const T* uin, T* uout, const T* f,
+                               double a_f, int colour, cudaStream_t s) {
+  const int pairs = (G.n2 + 1) / 2;
+  dim3 block(kPairX, kRowsY, 1);
+  dim3 grid((pairs + kPairX - 1) / kPairX, (G.n1 + kRowsY - 1) / kRowsY, G.n0);
+  switch (order) {
+    case 2: k_smooth_half<2, T><<<grid, block, 0, s>>>(G, uin, uout, f, T(a_f), colour); break;
+    case 4: k_smooth_half<4, T><<<grid, block, 0, s>>>(G, uin, uout, f, T(a_f), colour); break;
+    case 6: k_smooth_half<6, T><<<grid, block, 0, s>>>(G, uin, uout, f, T(a_f), colour); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_residual_restrict(int order, const Grid& F, const T* u, const T* f,
+                                     double invh2, const Grid& P, T* pu, T* pfas, T* ubar,
+                                     Int3 off, Int3 cn, cudaStream_t s) {
+  dim3 block(32, 4, 1);
+  dim3 grid = coarse_grid(cn, block);
+  switch (order) {
+    case 2: k_residual_restrict<2, T><<<grid, block, 0, s>>>(F, u, f, T(invh2), P, pu, pfas, ubar, off, cn); break;
+    case 4: k_residual_restrict<4, T><<<grid, block, 0, s>>>(F, u, f, T(invh2), P, pu, pfas, ubar, off, cn); break;
+    case 6: k_residual_restrict<6, T><<<grid, block, 0, s>>>(F, u, f, T(invh2), P, pu, pfas, ubar, off, cn); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_fas_source(int order, const Grid& P, const T* pu, T* pfas, double invH2,
+                              Int3 off, Int3 cn, cudaStream_t s) {
+  dim3 block(32, 4, 1);
+  dim3 grid = coarse_grid(cn, block);
+  switch (order) {
+    case 2: k_fas_source<2, T><<<grid, block, 0, s>>>(P, pu, pfas, T(invH2), off, cn); break;
+    case 4: k_fas_source<4, T><<<grid, block, 0, s>>>(P, pu, pfas, T(invH2), off, cn); break;
+    case 6: k_fas_source<6, T><<<grid, block, 0, s>>>(P, pu, pfas, T(invH2), off, cn); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_prolong(const Grid& F, T* u, const Grid& P, const T* pu, const T* ubar,
+                           Int3 off, Int3 cn, cudaStream_t s) {
+  dim3 block(32, 4, 1);
+  const int pairs = F.n2 / 2;
+  dim3 grid((pairs + 31) / 32, (F.n1 + 3) / 4, F.n0);
+  k_prolong<T><<<grid, block, 0, s>>>(F, u, P, pu, ubar, off, cn);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_restrict_u(const Grid& F, const T* u, const Grid& P, T* pu, Int3 off, Int3 cn,
+                              cudaStream_t s) {
+  dim3 block(32, 4, 1);
+  dim3 grid = coarse_grid(cn, block);
+  k_restrict_u<T><<<grid, block, 0, s>>>(F, u, P, pu, off, cn);
+  return cudaGetLastError();
+}
+
+#define MGK_INSTANTIATE(T)                                                                     \
+  template cudaError_t launch_smooth_half<T>(int, const Grid&, const T*, T*, const T*, double, \
+                                             int, cudaStream_t);                               \
+  template cudaError_t launch_residual_restrict<T>(int, const Grid&, const T*, const T*,       \
+                                                   double, const Grid&, T*, T*, T*, Int3,      \
+                                                   Int3, cudaStream_t);                        \
+  template cudaError_t launch_fas_source<T>(int, const Grid&, const T*, T*, double, Int3,      \
+                                            Int3, cudaStream_t);                               \
+  template cudaError_t launch_prolong<T>(const Grid&, T*, const Grid&, const T*, const T*,     \
+                                         Int3, Int3, cudaStream_t);                            \
+  template cudaError_t launch_restrict_u<T>(const Grid&, const T*, const Grid&, T*, Int3,      \
+                                            Int3, cudaStream_t);
+
+MGK_INSTANTIATE(double)
+MGK_INSTANTIATE(float)
+
+}  // namespace mgk

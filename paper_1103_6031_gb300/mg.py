@@ -1,0 +1,240 @@
+"""ctypes binding of the C ABI in include/mg.h (argument marshalling only).
+
+Every step of the solve runs in the CUDA library libmgic.so; this module only
+builds the config struct, passes device pointers of torch tensors and the
+current CUDA stream, and turns status codes into exceptions.  There is no CPU
+fallback: if the library cannot be loaded, every call raises.
+"""
+
+import ctypes
+import os
+
+MG_MAX_LEVELS = 16
+MG_MAX_HISTORY = 64
+MG_FP64 = 0
+MG_MIXED = 1
+
+STATUS = {0: "MG_OK", 1: "MG_EINVAL", 2: "MG_ENOMEM", 3: "MG_ENOCONV", 4: "MG_ECUDA",
+          5: "MG_ETIMEOUT"}
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class MGConfig(ctypes.Structure):
+    _fields_ = [
+        ("n_levels", ctypes.c_int),
+        ("base_n", ctypes.c_int * 3),
+        ("box", ctypes.c_double),
+        ("nest_n", (ctypes.c_int * 3) * (MG_MAX_LEVELS - 1)),
+        ("nest_off", (ctypes.c_int * 3) * (MG_MAX_LEVELS - 1)),
+        ("order", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("nu1", ctypes.c_int),
+        ("nu2", ctypes.c_int),
+        ("max_cycles", ctypes.c_int),
+        ("tol", ctypes.c_double),
+        ("dev_alloc", _ALLOC_FN),
+        ("dev_free", _FREE_FN),
+        ("alloc_ctx", ctypes.c_void_p),
+    ]
+
+
+class MGInfo(ctypes.Structure):
+    _fields_ = [
+        ("cycles", ctypes.c_int),
+        ("rel_residual", ctypes.c_double),
+        ("source_mean", ctypes.c_double),
+        ("history", ctypes.c_double * MG_MAX_HISTORY),
+    ]
+
+    def as_dict(self):
+        return {"cycles": self.cycles, "rel_residual": self.rel_residual,
+                "source_mean": self.source_mean,
+                "history": [self.history[i] for i in range(min(self.cycles, MG_MAX_HISTORY))]}
+
+
+class MGError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (STATUS.get(status, status), message))
+        self.status = status
+
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libmgic.so")
+_lib = None
+
+
+def load_library(path=None):
+    """Load libmgic.so (built by __graft_entry__.build()); raises if absent."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise OSError("libmgic.so not found at %s; run __graft_entry__.build() first" % p)
+    lib = ctypes.CDLL(p)
+    vp = ctypes.c_void_p
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "mg_config_default": (None, [ctypes.POINTER(MGConfig)]),
+        "mg_config_validate": (ctypes.c_int, [ctypes.POINTER(MGConfig), ctypes.c_char_p, ctypes.c_size_t]),
+        "mg_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(MGConfig)]),
+        "mg_total_levels": (ctypes.c_int, [ctypes.POINTER(MGConfig)]),
+        "mg_hierarchy_create": (ctypes.c_int, [ctypes.POINTER(MGConfig), vp, ctypes.POINTER(vp)]),
+        "mg_hierarchy_destroy": (ctypes.c_int, [vp]),
+        "mg_solve_1lpt": (ctypes.c_int, [vp, pp, pp, ctypes.POINTER(MGInfo)]),
+        "mg_solve_2lpt": (ctypes.c_int, [vp, pp, pp, ctypes.POINTER(MGInfo)]),
+        "mg_displacements": (ctypes.c_int, [vp, pp, pp]),
+        "mg_lpt2_source": (ctypes.c_int, [vp, pp, pp]),
+        "mg_lpt_pipeline": (ctypes.c_int, [vp, ctypes.c_int, pp, pp, pp, pp, pp,
+                                           ctypes.POINTER(MGInfo), ctypes.POINTER(MGInfo)]),
+        "mg_last_error": (ctypes.c_char_p, [vp]),
+        "mg_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def make_config(base_n, box, order, nests=(), precision=MG_FP64, nu1=2, nu2=2, max_cycles=50,
+                tol=1e-10):
+    """MGConfig from plain values; nests = [(n3, off3), ...] (off in parent cells)."""
+    lib = load_library()
+    cfg = MGConfig()
+    lib.mg_config_default(ctypes.byref(cfg))
+    cfg.n_levels = 1 + len(nests)
+    for a in range(3):
+        cfg.base_n[a] = int(base_n[a])
+    cfg.box = float(box)
+    for i, (n, off) in enumerate(nests):
+        for a in range(3):
+            cfg.nest_n[i][a] = int(n[a])
+            cfg.nest_off[i][a] = int(off[a])
+    cfg.order = int(order)
+    cfg.precision = int(precision)
+    cfg.nu1, cfg.nu2, cfg.max_cycles, cfg.tol = int(nu1), int(nu2), int(max_cycles), float(tol)
+    return cfg
+
+
+def config_from_geometry(geom, **kw):
+    return make_config(geom.base_n, geom.box, geom.order, [(n.n, n.off) for n in geom.nests], **kw)
+
+
+def validate(cfg):
+    lib = load_library()
+    buf = ctypes.create_string_buffer(512)
+    st = lib.mg_config_validate(ctypes.byref(cfg), buf, 512)
+    return st, buf.value.decode()
+
+
+def workspace_bytes(cfg):
+    return int(load_library().mg_workspace_bytes(ctypes.byref(cfg)))
+
+
+def _ptrs(tensors):
+    arr = (ctypes.c_void_p * len(tensors))()
+    for i, t in enumerate(tensors):
+        arr[i] = None if t is None else t.data_ptr()
+    return arr
+
+
+class Hierarchy:
+    """A device-resident hierarchy (opaque C handle) bound to a CUDA stream.
+
+    Inputs/outputs are torch float64 tensors on the GPU (or pinned CPU tensors
+    for pipeline(host=True)); all arithmetic happens in libmgic.so."""
+
+    def __init__(self, cfg, stream=None, torch_allocator=True):
+        import torch
+        self._torch = torch
+        self.lib = load_library()
+        self.cfg = cfg
+        self.shapes = [tuple(cfg.base_n)] + [tuple(cfg.nest_n[i]) for i in range(cfg.n_levels - 1)]
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._keep = []
+        if torch_allocator:
+            dev, strm = self.device.index, self.stream
+
+            def _alloc(nbytes, ctx):
+                return torch.cuda.caching_allocator_alloc(int(nbytes), dev, strm)
+
+            def _free(ptr, ctx):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            cfg.dev_alloc = _ALLOC_FN(_alloc)
+            cfg.dev_free = _FREE_FN(_free)
+            self._keep += [cfg.dev_alloc, cfg.dev_free]
+        handle = ctypes.c_void_p()
+        st = self.lib.mg_hierarchy_create(ctypes.byref(cfg), ctypes.c_void_p(self.stream.cuda_stream),
+                                          ctypes.byref(handle))
+        if st != 0:
+            raise MGError(st, "mg_hierarchy_create: " + validate(cfg)[1])
+        self.h = handle
+
+    def _check(self, st, what, allow_noconv=False):
+        if st == 0 or (allow_noconv and st == 3):
+            return
+        msg = self.lib.mg_last_error(self.h)
+        raise MGError(st, "%s: %s" % (what, msg.decode() if msg else ""))
+
+    def _empty(self, shape):
+        return self._torch.empty(shape, dtype=self._torch.float64, device=self.device)
+
+    def solve_1lpt(self, deltas, allow_noconv=False):
+        phis = [self._empty(s) for s in self.shapes]
+        info = MGInfo()
+        st = self.lib.mg_solve_1lpt(self.h, _ptrs(deltas), _ptrs(phis), ctypes.byref(info))
+        self._check(st, "mg_solve_1lpt", allow_noconv)
+        return phis, info.as_dict()
+
+    def solve_2lpt(self, phi1, allow_noconv=False):
+        phis = [self._empty(s) for s in self.shapes]
+        info = MGInfo()
+        st = self.lib.mg_solve_2lpt(self.h, _ptrs(phi1), _ptrs(phis), ctypes.byref(info))
+        self._check(st, "mg_solve_2lpt", allow_noconv)
+        return phis, info.as_dict()
+
+    def lpt2_source(self, phi1):
+        taus = [self._empty(s) for s in self.shapes]
+        st = self.lib.mg_lpt2_source(self.h, _ptrs(phi1), _ptrs(taus))
+        self._check(st, "mg_lpt2_source")
+        return taus
+
+    def displacements(self, phi):
+        disp = [[self._empty(s) for _ in range(3)] for s in self.shapes]
+        flat = [d for level in disp for d in level]
+        st = self.lib.mg_displacements(self.h, _ptrs(phi), _ptrs(flat))
+        self._check(st, "mg_displacements")
+        return disp
+
+    def pipeline(self, deltas, outputs=None, host=False, allow_noconv=False):
+        """Whole step; `outputs` = dict of preallocated lists (phi1, phi2, disp1, disp2)."""
+        if outputs is None:
+            mk = (lambda s: self._torch.empty(s, dtype=self._torch.float64, pin_memory=True)) if host \
+                else self._empty
+            outputs = {"phi1": [mk(s) for s in self.shapes], "phi2": [mk(s) for s in self.shapes],
+                       "disp1": [mk(s) for s in self.shapes for _ in range(3)],
+                       "disp2": [mk(s) for s in self.shapes for _ in range(3)]}
+        i1, i2 = MGInfo(), MGInfo()
+        st = self.lib.mg_lpt_pipeline(self.h, 1 if host else 0, _ptrs(deltas),
+                                      _ptrs(outputs["phi1"]), _ptrs(outputs["phi2"]),
+                                      _ptrs(outputs["disp1"]), _ptrs(outputs["disp2"]),
+                                      ctypes.byref(i1), ctypes.byref(i2))
+        self._check(st, "mg_lpt_pipeline", allow_noconv)
+        return outputs, i1.as_dict(), i2.as_dict()
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mg_hierarchy_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Benchmark of the nested-grid initial-conditions step on GB300.
+
+One step = the whole hot path on one hierarchy: 1LPT solve of L phi1 = delta,
+2LPT source tau(phi1), 2LPT solve of L phi2 = tau, displacements -G phi1 and
+-G phi2 (float64, order-6 operators).  Workload: 128^3 periodic base of a
+100 Mpc/h box plus one centred 128^3 nest at twice the resolution (4,194,304
+level-cells), BBKS density at z = 50 from seeded white noise.  Each solve
+stops at a relative leaf residual of 1e-7, which gives <= 1e-6 RMS relative
+error in phi and in the displacements (checked by the GPU tests).
+
+Default: N = 1, 10 timed steps after 3 warm-up steps.  Under torchrun every
+rank solves its own hierarchy (replicas, no collective in the data path);
+value = level-cells of all ranks / max-over-ranks time.
+
+--impl reference times the CPU oracle on a bounded sample of the same
+workload (one V-cycle per step, scaled to the cycles of a full step).
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "level-cells solved/s to 1e-6 rel. error; % HBM peak; p50/p99 solve latency"
+UNIT = "level-cells/s"
+SOLVE_TOL = 1e-7
+SEED = 2
+# V-cycles of one full step at SOLVE_TOL on this workload (1LPT + 2LPT), as the
+# GPU arm reports them; the oracle arm scales its one-cycle sample by this.
+CYCLES_PER_STEP = 14
+FP64_PEAK_GOPS = 625.0   # nominal 1.25 TFLOP/s FP64 = 625 G FP64 instructions/s
+L2_FLUSH_BYTES = 256 << 20
+
+# smoother: FP64 instructions per updated cell (three 6-neighbour sums: 15 adds,
+# a_f * f: 1 multiply, 3 fused multiply-adds) for the order-6 stencil
+SMOOTH_OPS_PER_UPDATE = {2: 7, 4: 13, 6: 19}
+# in-place algorithmic bytes of one colour half-sweep per level-cell: read u of
+# both colours (8 B), f of the updated colour (4 B), write the updated colour (4 B)
+SMOOTH_BYTES_PER_CELL = 16.0
+
+
+def workload():
+    from synthetic import config_zoom2
+    return config_zoom2()
+
+
+def workload_config(geom):
+    return {"workload": "zoom2: 128^3 periodic base (100 Mpc/h) + centred 128^3 nest at 2x, "
+                        "order-6 FD, FP64, 1LPT+2LPT+displacements, BBKS z=50, seed %d" % SEED,
+            "level_cells": geom.level_cells(), "order": geom.order, "levels": geom.n_levels,
+            "solve_tol": SOLVE_TOL, "precision": "fp64",
+            "l2": "256 MiB flush written between timed steps, outside the per-step events"}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reduce_max(value, dist, device):
+    """Max over ranks of a float (identity when not distributed)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(value, dist, device):
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def aggregate(local_ms_total, local_units, steps, dist, device):
+    """Whole-job throughput: units of all ranks / max-over-ranks timed span."""
+    span_ms = reduce_max(local_ms_total, dist, device)
+    units = reduce_sum(local_units, dist, device)
+    return units / (span_ms / 1e3), span_ms / steps
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def cpu_baseline(geom, deltas, cycles_per_step):
+    """The oracle on the host cores: one V-cycle, tau and one gradient of the
+    same hierarchy, scaled to a full step (cycles_per_step cycles, tau, two
+    gradients)."""
+    from oracle.hierarchy import Hierarchy
+    from oracle.lpt import gradient, lpt2_source
+    from oracle.multigrid import solve
+    t0 = time.perf_counter()
+    phis, _ = solve(geom, deltas, tol=0.0, cycles=1)
+    t_cycle = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    lpt2_source(Hierarchy(geom), phis)
+    t_tau = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    gradient(Hierarchy(geom), phis)
+    t_grad = time.perf_counter() - t0
+    t_step = cycles_per_step * t_cycle + t_tau + 2 * t_grad
+    return {"value": geom.level_cells() / t_step, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "1 V-cycle (%.1f s) + tau (%.1f s) + 1 gradient (%.1f s) of the same "
+                      "hierarchy on one host core (numpy), scaled to %d cycles + tau + 2 "
+                      "gradients" % (t_cycle, t_tau, t_grad, cycles_per_step)}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np  # noqa: F401
+    from oracle.hierarchy import Hierarchy
+    from oracle.lpt import gradient, lpt2_source
+    from oracle.multigrid import solve
+    from synthetic import make_delta
+    geom = workload()
+    deltas = make_delta(geom, SEED)
+    extra = 0.0
+    for w in range(args.warmup):
+        phis, _ = solve(geom, deltas, tol=0.0, cycles=1)
+        if w == 0:
+            t0 = time.perf_counter()
+            lpt2_source(Hierarchy(geom), phis)
+            gradient(Hierarchy(geom), phis)
+            gradient(Hierarchy(geom), phis)
+            extra = time.perf_counter() - t0
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        solve(geom, deltas, tol=0.0, cycles=1)
+        times.append(time.perf_counter() - t0)
+    t_cycle = statistics.mean(times)
+    t_step = CYCLES_PER_STEP * t_cycle + extra
+    value = geom.level_cells() / t_step
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(geom), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "each step: 1 V-cycle of the FP64 numpy oracle (mean %.2f s); "
+                                       "reported per full step = %d cycles + tau + 2 gradients "
+                                       "(%.1f s, timed once in warm-up)"
+                                       % (t_cycle, CYCLES_PER_STEP, extra)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+        dist = tdist
+    else:
+        torch.cuda.set_device(0)
+    device = torch.device("cuda", torch.cuda.current_device())
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1103_6031_gb300 as pkg
+    from synthetic import make_delta
+
+    geom = workload()
+    deltas_np = make_delta(geom, SEED)
+    cfg = pkg.config_from_geometry(geom, tol=SOLVE_TOL, max_cycles=50)
+    h = pkg.Hierarchy(cfg)
+    stream = h.stream
+    deltas = [torch.from_numpy(x).to(device) for x in deltas_np]
+    shapes = h.shapes
+    out = {"phi1": [torch.empty(s, dtype=torch.float64, device=device) for s in shapes],
+           "phi2": [torch.empty(s, dtype=torch.float64, device=device) for s in shapes],
+           "disp1": [torch.empty(s, dtype=torch.float64, device=device) for s in shapes for _ in range(3)],
+           "disp2": [torch.empty(s, dtype=torch.float64, device=device) for s in shapes for _ in range(3)]}
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    info1 = info2 = None
+    for w in range(args.warmup):
+        _, info1, info2 = h.pipeline(deltas, out)
+    h.stats(reset=True)
+    h.set_profiling(["smooth"])
+    sampler = ClockSampler(device.index)
+    sampler.start()
+    time.sleep(0.4)
+    barrier()
+    evs = []
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, info1, info2 = h.pipeline(deltas, out)
+        b.record(stream)
+        evs.append((a, b))
+    barrier()
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    stats = h.stats(reset=True)
+    h.set_profiling([])
+    value, ms_per_step = aggregate(sum(step_ms), geom.level_cells() * args.steps, args.steps,
+                                   dist, device)
+    launches = sum(v["launches"] for v in stats.values())
+    sm = stats["smooth"]
+    updates_per_launch = sm["cells"] / max(sm["launches"], 1)
+    ms_per_launch = sm["event_ms"] / max(sm["timed"], 1)
+    ops = SMOOTH_OPS_PER_UPDATE[geom.order] * updates_per_launch
+    achieved_gops = ops / (ms_per_launch * 1e-3) / 1e9
+    smooth_gbs = SMOOTH_BYTES_PER_CELL * 2 * updates_per_launch / (ms_per_launch * 1e-3) / 1e9
+    total_smooth_ms = sm["event_ms"]
+
+    if args.profile_run:
+        if rank == 0:
+            print(json.dumps({"profile_run": True, "value": value, "ms_per_step": ms_per_step,
+                              "gpu_launches": launches, "cycles": [info1["cycles"], info2["cycles"]]}))
+        h.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    # end to end through the C ABI with pinned host buffers
+    host_in = [torch.from_numpy(x).pin_memory() for x in deltas_np]
+    host_out = {"phi1": [torch.empty(s, dtype=torch.float64, pin_memory=True) for s in shapes],
+                "phi2": [torch.empty(s, dtype=torch.float64, pin_memory=True) for s in shapes],
+                "disp1": [torch.empty(s, dtype=torch.float64, pin_memory=True) for s in shapes for _ in range(3)],
+                "disp2": [torch.empty(s, dtype=torch.float64, pin_memory=True) for s in shapes for _ in range(3)]}
+    h.pipeline(host_in, host_out, host=True)
+    barrier()
+    e2e_ms = []
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h.pipeline(host_in, host_out, host=True)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    barrier()
+    e2e_value, _ = aggregate(sum(e2e_ms), geom.level_cells() * args.steps, args.steps, dist, device)
+    h2d = sum(x.numel() * 8 for x in host_in)
+    d2h = sum(x.numel() * 8 for k in host_out for x in host_out[k])
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(geom),
+            "latency_ms": {"p50": statistics.median(step_ms),
+                           "p99": sorted(step_ms)[max(0, int(round(0.99 * len(step_ms))) - 1)]},
+            "cycles": {"1lpt": info1["cycles"], "2lpt": info2["cycles"],
+                       "rel_residual_1lpt": info1["rel_residual"],
+                       "rel_residual_2lpt": info2["rel_residual"]},
+            "roofline": {"bound": "alu", "achieved": achieved_gops, "peak": FP64_PEAK_GOPS,
+                         "unit": "G FP64 instr/s", "frac": achieved_gops / FP64_PEAK_GOPS,
+                         "traffic": None, "kernel": "k_smooth_half<6,double>",
+                         "peak_source": "nominal FP64 1.25 TFLOP/s (recipe) = 625 G FMA/s",
+                         "ms_per_launch": ms_per_launch, "updates_per_launch": updates_per_launch,
+                         "hbm_view": {"achieved_gbs": smooth_gbs, "peak_gbs": 6765.0,
+                                      "frac": smooth_gbs / 6765.0,
+                                      "bytes_per_cell": SMOOTH_BYTES_PER_CELL},
+                         "share_of_step": total_smooth_ms / max(sum(step_ms), 1e-9)},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h,
+                    "ms_per_step": statistics.mean(e2e_ms)},
+        }
+        if not args.skip_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(geom, deltas_np, info1["cycles"] + info2["cycles"])
+        print(json.dumps(line))
+    h.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--skip-baseline", action="store_true",
+                    help="leave out the CPU-oracle baseline")
+    ap.add_argument("--profile-run", action="store_true",
+                    help="timed steps only: no end-to-end pass, no CPU baseline (for ncu)")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -132,6 +132,36 @@ mg_status mg_lpt_pipeline(mg_hierarchy* h, int host_buffers, const double* const
                           double* const phi1[], double* const phi2[], double* const disp1[],
                           double* const disp2[], mg_info* info1, mg_info* info2);
 
+/* Kernel families for launch counting and event timing. */
+typedef enum {
+  MG_K_SMOOTH = 0,     /* red-black half-sweep                                 */
+  MG_K_RESTRICT = 1,   /* residual + restriction, restriction of u             */
+  MG_K_FAS = 2,        /* FAS source on covered parent cells                   */
+  MG_K_PROLONG = 3,    /* prolongation-correction                              */
+  MG_K_GHOST = 4,      /* periodic ghosts, coarse-fine interpolation and flux  */
+  MG_K_COARSEST = 5,   /* exact solve on the coarsest level                    */
+  MG_K_NORM = 6,       /* residual norms, composite mean, reductions           */
+  MG_K_LPT = 7,        /* 2LPT source and gradient                             */
+  MG_K_COPY = 8,       /* packing, fills                                       */
+  MG_K_FAMILIES = 9
+} mg_kernel_family;
+
+typedef struct {
+  long long launches[MG_K_FAMILIES];  /* kernel launches since the last reset            */
+  long long cells[MG_K_FAMILIES];     /* cells each family processed (smooth: updated)    */
+  double event_ms[MG_K_FAMILIES];     /* summed CUDA-event time of timed launches         */
+  long long timed[MG_K_FAMILIES];     /* launches that carried events                     */
+} mg_stats;
+
+/* Time every launch of the families in mask (bit f = family f) with a CUDA
+ * event pair on the hierarchy's stream (0 disables).  Adds two event records
+ * per timed launch. */
+mg_status mg_set_profiling(mg_hierarchy* h, unsigned mask);
+
+/* Copy the counters out (synchronising the stream to read event times) and,
+ * if reset != 0, zero them. */
+mg_status mg_get_stats(mg_hierarchy* h, mg_stats* out, int reset);
+
 /* Message for the last failing call on h ("" if none; NULL-safe). */
 const char* mg_last_error(const mg_hierarchy* h);
 

@@ -78,6 +78,11 @@ struct mg_hierarchy {
   double* scratch = nullptr;   // 3 dense arrays of the largest leaf level
   long long scratch_elems = 0;
   double volume = 0.0;
+  // launch counters and optional CUDA-event timing per kernel family
+  mg_stats stats;
+  unsigned prof_mask = 0;
+  std::vector<cudaEvent_t> ev_start[MG_K_FAMILIES], ev_end[MG_K_FAMILIES];
+  size_t ev_used[MG_K_FAMILIES] = {0};
 };
 
 namespace {
@@ -104,6 +109,45 @@ mg_status fail_cuda(mg_hierarchy* h, cudaError_t e, const char* what) {
     mg_status st_ = (expr);            \
     if (st_ != MG_OK) return st_;      \
   } while (0)
+
+mg_status prof_begin(mg_hierarchy* h, int fam) {
+  if (!(h->prof_mask & (1u << fam))) return MG_OK;
+  size_t& used = h->ev_used[fam];
+  if (used == h->ev_start[fam].size()) {
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    h->ev_start[fam].push_back(a);
+    h->ev_end[fam].push_back(b);
+  }
+  CK(cudaEventRecord(h->ev_start[fam][used], h->s));
+  return MG_OK;
+}
+
+mg_status prof_end(mg_hierarchy* h, int fam, long long cells) {
+  h->stats.launches[fam] += 1;
+  h->stats.cells[fam] += cells;
+  if (!(h->prof_mask & (1u << fam))) return MG_OK;
+  size_t& used = h->ev_used[fam];
+  CK(cudaEventRecord(h->ev_end[fam][used], h->s));
+  used += 1;
+  return MG_OK;
+}
+
+// Launch a kernel of family `fam` that processes `cells` cells, counted and
+// (when profiling is on for the family) bracketed by CUDA events.
+#define KL(fam, cells, expr)              \
+  do {                                    \
+    ST(prof_begin(h, (fam)));             \
+    CK(expr);                             \
+    ST(prof_end(h, (fam), (cells)));      \
+  } while (0)
+
+long long cells_of(const Grid& G) { return (long long)G.n0 * G.n1 * G.n2; }
+long long cells_of(Int3 c) { return (long long)c.x * c.y * c.z; }
+long long shell_of(const Grid& G) {
+  return (long long)G.X * G.Y * (G.n2 + 2 * G.g) - cells_of(G);
+}
 
 bool validate(const mg_config* cfg, char* msg, size_t len, Plan* plan) {
   if (!cfg) {
@@ -192,7 +236,7 @@ bool validate(const mg_config* cfg, char* msg, size_t len, Plan* plan) {
 mg_status tangential(mg_hierarchy* h, int l) {
   DevLevel& L = h->L[l];
   DevLevel& P = h->L[l - 1];
-  CK(launch_cf_tangential<double>(h->cfg.order, L.G, P.G, P.u[P.cur], L.off, L.fs, h->w,
+  KL(MG_K_GHOST, L.fs.base[6], launch_cf_tangential<double>(h->cfg.order, L.G, P.G, P.u[P.cur], L.off, L.fs, h->w,
                                   1.0 / P.geo.h, L.inter, L.fc_unc, h->s));
   return MG_OK;
 }
@@ -200,14 +244,14 @@ mg_status tangential(mg_hierarchy* h, int l) {
 mg_status ghost_fill(mg_hierarchy* h, int l, bool edges) {
   DevLevel& L = h->L[l];
   if (L.periodic) {
-    CK(launch_ghost_periodic<double>(L.G, L.u[L.cur], h->s));
+    KL(MG_K_GHOST, shell_of(L.G), launch_ghost_periodic<double>(L.G, L.u[L.cur], h->s));
     return MG_OK;
   }
   DevLevel& P = h->L[l - 1];
-  CK(launch_cf_flux<double>(h->cfg.order, L.G, L.u[L.cur], L.fs, h->w, L.inter, L.fc_unc,
+  KL(MG_K_GHOST, 4 * L.fs.ebase[6] * L.G.g, launch_cf_flux<double>(h->cfg.order, L.G, L.u[L.cur], L.fs, h->w, L.inter, L.fc_unc,
                             L.geo.h, 1.0 / L.geo.h, 1.0 / P.geo.h, 1, h->s));
   if (edges)
-    CK(launch_cf_edges<double>(h->cfg.order, L.G, L.u[L.cur], P.G, P.u[P.cur], L.off, h->w, h->s));
+    KL(MG_K_GHOST, shell_of(L.G), launch_cf_edges<double>(h->cfg.order, L.G, L.u[L.cur], P.G, P.u[P.cur], L.off, h->w, h->s));
   return MG_OK;
 }
 
@@ -215,7 +259,7 @@ mg_status half_sweep(mg_hierarchy* h, int l, int colour) {
   DevLevel& L = h->L[l];
   ST(ghost_fill(h, l, false));
   const double a_f = L.geo.h * L.geo.h / centre_weight(h->cfg.order);
-  CK(launch_smooth_half<double>(h->cfg.order, L.G, L.u[L.cur], L.u[1 - L.cur], L.ffas, a_f,
+  KL(MG_K_SMOOTH, (cells_of(L.G) + 1) / 2, launch_smooth_half<double>(h->cfg.order, L.G, L.u[L.cur], L.u[1 - L.cur], L.ffas, a_f,
                                 colour, h->s));
   L.cur ^= 1;
   return MG_OK;
@@ -233,21 +277,21 @@ mg_status vcycle(mg_hierarchy* h, int l) {
   DevLevel& L = h->L[l];
   const int order = h->cfg.order;
   if (l == 0) {
-    CK(launch_coarsest(L.G, L.ffas, L.u[L.cur], L.kern, h->s));
-    CK(launch_ghost_periodic<double>(L.G, L.u[L.cur], h->s));
+    KL(MG_K_COARSEST, cells_of(L.G), launch_coarsest(L.G, L.ffas, L.u[L.cur], L.kern, h->s));
+    KL(MG_K_GHOST, shell_of(L.G), launch_ghost_periodic<double>(L.G, L.u[L.cur], h->s));
     return MG_OK;
   }
   DevLevel& P = h->L[l - 1];
   ST(smooth(h, l, h->cfg.nu1));
   ST(ghost_fill(h, l, false));
-  CK(launch_residual_restrict<double>(order, L.G, L.u[L.cur], L.ffas, 1.0 / (L.geo.h * L.geo.h),
+  KL(MG_K_RESTRICT, cells_of(L.G), launch_residual_restrict<double>(order, L.G, L.u[L.cur], L.ffas, 1.0 / (L.geo.h * L.geo.h),
                                       P.G, P.u[P.cur], P.ffas, L.ubar, L.off, L.cn, h->s));
-  if (P.periodic) CK(launch_ghost_periodic<double>(P.G, P.u[P.cur], h->s));
-  CK(launch_fas_source<double>(order, P.G, P.u[P.cur], P.ffas, 1.0 / (P.geo.h * P.geo.h), L.off,
+  if (P.periodic) KL(MG_K_GHOST, shell_of(P.G), launch_ghost_periodic<double>(P.G, P.u[P.cur], h->s));
+  KL(MG_K_FAS, cells_of(L.cn), launch_fas_source<double>(order, P.G, P.u[P.cur], P.ffas, 1.0 / (P.geo.h * P.geo.h), L.off,
                                L.cn, h->s));
   ST(vcycle(h, l - 1));
   if (!L.periodic) ST(tangential(h, l));
-  CK(launch_prolong<double>(L.G, L.u[L.cur], P.G, P.u[P.cur], L.ubar, L.off, L.cn, h->s));
+  KL(MG_K_PROLONG, cells_of(L.G), launch_prolong<double>(L.G, L.u[L.cur], P.G, P.u[P.cur], L.ubar, L.off, L.cn, h->s));
   ST(smooth(h, l, h->cfg.nu2));
   return MG_OK;
 }
@@ -258,7 +302,7 @@ mg_status sync_covered(mg_hierarchy* h) {
   for (int l = finest(h); l > h->base; --l) {
     DevLevel& L = h->L[l];
     DevLevel& P = h->L[l - 1];
-    CK(launch_restrict_u<double>(L.G, L.u[L.cur], P.G, P.u[P.cur], L.off, L.cn, h->s));
+    KL(MG_K_RESTRICT, cells_of(L.G), launch_restrict_u<double>(L.G, L.u[L.cur], P.G, P.u[P.cur], L.off, L.cn, h->s));
   }
   return MG_OK;
 }
@@ -269,11 +313,11 @@ mg_status leaf_norms(mg_hierarchy* h, double* rr, double* ff, double* fsum) {
   for (int l = h->base; l <= finest(h); ++l) {
     DevLevel& L = h->L[l];
     ST(ghost_fill(h, l, false));
-    CK(launch_norm_partial(h->cfg.order, L.G, L.u[L.cur], L.f, 1.0 / (L.geo.h * L.geo.h),
+    KL(MG_K_NORM, cells_of(L.G), launch_norm_partial(h->cfg.order, L.G, L.u[L.cur], L.f, 1.0 / (L.geo.h * L.geo.h),
                            L.geo.h * L.geo.h * L.geo.h, L.child_lo, L.child_hi,
                            h->partial + 2 * L.partial_off, L.nblocks, h->s));
   }
-  CK(launch_reduce_partials(h->partial, h->partial_slots, 2, h->red, h->s));
+  KL(MG_K_NORM, h->partial_slots, launch_reduce_partials(h->partial, h->partial_slots, 2, h->red, h->s));
   CK(cudaMemcpyAsync(h->host_red, h->red, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->s));
   CK(cudaStreamSynchronize(h->s));
   *rr = h->host_red[0];
@@ -286,19 +330,19 @@ mg_status leaf_norms(mg_hierarchy* h, double* rr, double* ff, double* fsum) {
 mg_status solve_prepared(mg_hierarchy* h, mg_info* info) {
   for (int l = h->base; l <= finest(h); ++l) {
     DevLevel& L = h->L[l];
-    CK(launch_sum_partial(L.G, L.f, L.geo.h * L.geo.h * L.geo.h, L.child_lo, L.child_hi,
+    KL(MG_K_NORM, cells_of(L.G), launch_sum_partial(L.G, L.f, L.geo.h * L.geo.h * L.geo.h, L.child_lo, L.child_hi,
                           h->partial + 2 * L.partial_off, L.nblocks, h->s));
   }
-  CK(launch_reduce_partials(h->partial, h->partial_slots, 2, h->red + 2, h->s));
+  KL(MG_K_NORM, h->partial_slots, launch_reduce_partials(h->partial, h->partial_slots, 2, h->red + 2, h->s));
   for (int l = h->base; l <= finest(h); ++l) {
     DevLevel& L = h->L[l];
-    CK(launch_shift_copy(L.G, L.f, L.ffas, h->red + 2, 1.0 / h->volume, h->s));
+    KL(MG_K_COPY, cells_of(L.G), launch_shift_copy(L.G, L.f, L.ffas, h->red + 2, 1.0 / h->volume, h->s));
   }
   for (size_t l = 0; l < h->L.size(); ++l) {
     DevLevel& L = h->L[l];
     const long long e = grid_elems(L.G);
-    CK(launch_fill(L.u[0], e, 0.0, h->s));
-    CK(launch_fill(L.u[1], e, 0.0, h->s));
+    KL(MG_K_COPY, e, launch_fill(L.u[0], e, 0.0, h->s));
+    KL(MG_K_COPY, e, launch_fill(L.u[1], e, 0.0, h->s));
     L.cur = 0;
   }
   for (int l = h->base + 1; l <= finest(h); ++l) ST(tangential(h, l));
@@ -354,7 +398,7 @@ mg_status load_leaf(mg_hierarchy* h, int l, const double* src, double* padded, b
     cudaMemcpy3DParms p = dense_padded_parms(L, padded, const_cast<double*>(src), true);
     CK(cudaMemcpy3DAsync(&p, h->s));
   } else {
-    CK(launch_pack(L.G, src, padded, 0.0, h->s));
+    KL(MG_K_COPY, cells_of(L.G), launch_pack(L.G, src, padded, 0.0, h->s));
   }
   return MG_OK;
 }
@@ -365,7 +409,7 @@ mg_status store_leaf(mg_hierarchy* h, int l, const double* padded, double* dst, 
     cudaMemcpy3DParms p = dense_padded_parms(L, const_cast<double*>(padded), dst, false);
     CK(cudaMemcpy3DAsync(&p, h->s));
   } else {
-    CK(launch_unpack(L.G, padded, dst, h->s));
+    KL(MG_K_COPY, cells_of(L.G), launch_unpack(L.G, padded, dst, h->s));
   }
   return MG_OK;
 }
@@ -386,12 +430,12 @@ mg_status tau_into_f(mg_hierarchy* h) {
   for (int l = h->base; l <= finest(h); ++l) {
     DevLevel& L = h->L[l];
     ST(ghost_fill(h, l, true));
-    CK(launch_lpt2_source(h->cfg.order, L.G, L.u[L.cur], 1.0 / (L.geo.h * L.geo.h), L.f, h->s));
+    KL(MG_K_LPT, cells_of(L.G), launch_lpt2_source(h->cfg.order, L.G, L.u[L.cur], 1.0 / (L.geo.h * L.geo.h), L.f, h->s));
   }
   for (int l = finest(h); l > h->base; --l) {
     DevLevel& L = h->L[l];
     DevLevel& P = h->L[l - 1];
-    CK(launch_restrict_u<double>(L.G, L.f, P.G, P.f, L.off, L.cn, h->s));
+    KL(MG_K_RESTRICT, cells_of(L.G), launch_restrict_u<double>(L.G, L.f, P.G, P.f, L.off, L.cn, h->s));
   }
   return MG_OK;
 }
@@ -408,7 +452,7 @@ mg_status gradient_out(mg_hierarchy* h, double* const disp[], bool host) {
     const long long n = (long long)L.G.n0 * L.G.n1 * L.G.n2;
     if (host) {
       if (!dx && !dy && !dz) continue;
-      CK(launch_gradient(h->cfg.order, L.G, L.u[L.cur], 1.0 / L.geo.h, h->scratch,
+      KL(MG_K_LPT, n, launch_gradient(h->cfg.order, L.G, L.u[L.cur], 1.0 / L.geo.h, h->scratch,
                          h->scratch + n, h->scratch + 2 * n, h->s));
       for (int a = 0; a < 3; ++a)
         if (disp[3 * i + a])
@@ -416,7 +460,7 @@ mg_status gradient_out(mg_hierarchy* h, double* const disp[], bool host) {
                              cudaMemcpyDeviceToHost, h->s));
     } else {
       if (!dx || !dy || !dz) return fail(h, MG_EINVAL, "displacement output pointer is NULL");
-      CK(launch_gradient(h->cfg.order, L.G, L.u[L.cur], 1.0 / L.geo.h, dx, dy, dz, h->s));
+      KL(MG_K_LPT, n, launch_gradient(h->cfg.order, L.G, L.u[L.cur], 1.0 / L.geo.h, dx, dy, dz, h->s));
     }
   }
   return MG_OK;
@@ -471,6 +515,29 @@ int mg_total_levels(const mg_config* cfg) {
 
 const char* mg_version(void) { return "mgic-gb300 0.1 (sm_103a)"; }
 
+mg_status mg_set_profiling(mg_hierarchy* h, unsigned mask) {
+  if (!h) return MG_EINVAL;
+  h->prof_mask = mask & ((1u << MG_K_FAMILIES) - 1u);
+  return MG_OK;
+}
+
+mg_status mg_get_stats(mg_hierarchy* h, mg_stats* out, int reset) {
+  if (!h || !out) return MG_EINVAL;
+  CK(cudaStreamSynchronize(h->s));
+  for (int f = 0; f < MG_K_FAMILIES; ++f) {
+    for (size_t i = 0; i < h->ev_used[f]; ++i) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, h->ev_start[f][i], h->ev_end[f][i]));
+      h->stats.event_ms[f] += ms;
+    }
+    h->stats.timed[f] += (long long)h->ev_used[f];
+    h->ev_used[f] = 0;
+  }
+  *out = h->stats;
+  if (reset) std::memset(&h->stats, 0, sizeof(h->stats));
+  return MG_OK;
+}
+
 const char* mg_last_error(const mg_hierarchy* h) { return h ? h->err.c_str() : ""; }
 
 mg_status mg_hierarchy_create(const mg_config* cfg, void* cuda_stream, mg_hierarchy** out) {
@@ -480,6 +547,7 @@ mg_status mg_hierarchy_create(const mg_config* cfg, void* cuda_stream, mg_hierar
   char msg[256];
   if (!validate(cfg, msg, sizeof(msg), &plan)) return MG_EINVAL;
   mg_hierarchy* h = new mg_hierarchy();
+  std::memset(&h->stats, 0, sizeof(h->stats));
   h->cfg = *cfg;
   h->s = (cudaStream_t)cuda_stream;
   h->base = plan.base;
@@ -583,6 +651,10 @@ mg_status mg_hierarchy_destroy(mg_hierarchy* h) {
     else cudaFree(h->arena);
   }
   if (h->host_red) cudaFreeHost(h->host_red);
+  for (int f = 0; f < MG_K_FAMILIES; ++f) {
+    for (cudaEvent_t e : h->ev_start[f]) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->ev_end[f]) cudaEventDestroy(e);
+  }
   delete h;
   return MG_OK;
 }

@@ -54,6 +54,24 @@ class MGInfo(ctypes.Structure):
                 "history": [self.history[i] for i in range(min(self.cycles, MG_MAX_HISTORY))]}
 
 
+MG_K_FAMILIES = 9
+FAMILY_NAMES = ["smooth", "restrict", "fas", "prolong", "ghost", "coarsest", "norm", "lpt", "copy"]
+
+
+class MGStats(ctypes.Structure):
+    _fields_ = [
+        ("launches", ctypes.c_longlong * MG_K_FAMILIES),
+        ("cells", ctypes.c_longlong * MG_K_FAMILIES),
+        ("event_ms", ctypes.c_double * MG_K_FAMILIES),
+        ("timed", ctypes.c_longlong * MG_K_FAMILIES),
+    ]
+
+    def as_dict(self):
+        return {name: {"launches": self.launches[i], "cells": self.cells[i],
+                       "event_ms": self.event_ms[i], "timed": self.timed[i]}
+                for i, name in enumerate(FAMILY_NAMES)}
+
+
 class MGError(RuntimeError):
     def __init__(self, status, message):
         super().__init__("%s: %s" % (STATUS.get(status, status), message))
@@ -88,6 +106,8 @@ def load_library(path=None):
         "mg_lpt2_source": (ctypes.c_int, [vp, pp, pp]),
         "mg_lpt_pipeline": (ctypes.c_int, [vp, ctypes.c_int, pp, pp, pp, pp, pp,
                                            ctypes.POINTER(MGInfo), ctypes.POINTER(MGInfo)]),
+        "mg_set_profiling": (ctypes.c_int, [vp, ctypes.c_uint]),
+        "mg_get_stats": (ctypes.c_int, [vp, ctypes.POINTER(MGStats), ctypes.c_int]),
         "mg_last_error": (ctypes.c_char_p, [vp]),
         "mg_version": (ctypes.c_char_p, []),
     }
@@ -135,10 +155,26 @@ def workspace_bytes(cfg):
     return int(load_library().mg_workspace_bytes(ctypes.byref(cfg)))
 
 
-def _ptrs(tensors):
+def _ptrs(tensors, shapes=None, host=False):
+    """Array of raw pointers; every tensor must be a contiguous float64 tensor of
+    the level's shape, on the GPU (or in pinned host memory when host=True)."""
     arr = (ctypes.c_void_p * len(tensors))()
     for i, t in enumerate(tensors):
-        arr[i] = None if t is None else t.data_ptr()
+        if t is None:
+            arr[i] = None
+            continue
+        if str(t.dtype) != "torch.float64":
+            raise ValueError("tensor %d: dtype %s, expected float64" % (i, t.dtype))
+        if not t.is_contiguous():
+            raise ValueError("tensor %d is not contiguous" % i)
+        if host:
+            if t.is_cuda or not t.is_pinned():
+                raise ValueError("tensor %d: host buffers must be pinned CPU tensors" % i)
+        elif not t.is_cuda:
+            raise ValueError("tensor %d: expected a CUDA tensor" % i)
+        if shapes is not None and tuple(t.shape) != tuple(shapes[i]):
+            raise ValueError("tensor %d: shape %s, expected %s" % (i, tuple(t.shape), shapes[i]))
+        arr[i] = t.data_ptr()
     return arr
 
 
@@ -188,27 +224,27 @@ class Hierarchy:
     def solve_1lpt(self, deltas, allow_noconv=False):
         phis = [self._empty(s) for s in self.shapes]
         info = MGInfo()
-        st = self.lib.mg_solve_1lpt(self.h, _ptrs(deltas), _ptrs(phis), ctypes.byref(info))
+        st = self.lib.mg_solve_1lpt(self.h, _ptrs(deltas, self.shapes), _ptrs(phis), ctypes.byref(info))
         self._check(st, "mg_solve_1lpt", allow_noconv)
         return phis, info.as_dict()
 
     def solve_2lpt(self, phi1, allow_noconv=False):
         phis = [self._empty(s) for s in self.shapes]
         info = MGInfo()
-        st = self.lib.mg_solve_2lpt(self.h, _ptrs(phi1), _ptrs(phis), ctypes.byref(info))
+        st = self.lib.mg_solve_2lpt(self.h, _ptrs(phi1, self.shapes), _ptrs(phis), ctypes.byref(info))
         self._check(st, "mg_solve_2lpt", allow_noconv)
         return phis, info.as_dict()
 
     def lpt2_source(self, phi1):
         taus = [self._empty(s) for s in self.shapes]
-        st = self.lib.mg_lpt2_source(self.h, _ptrs(phi1), _ptrs(taus))
+        st = self.lib.mg_lpt2_source(self.h, _ptrs(phi1, self.shapes), _ptrs(taus))
         self._check(st, "mg_lpt2_source")
         return taus
 
     def displacements(self, phi):
         disp = [[self._empty(s) for _ in range(3)] for s in self.shapes]
         flat = [d for level in disp for d in level]
-        st = self.lib.mg_displacements(self.h, _ptrs(phi), _ptrs(flat))
+        st = self.lib.mg_displacements(self.h, _ptrs(phi, self.shapes), _ptrs(flat))
         self._check(st, "mg_displacements")
         return disp
 
@@ -221,12 +257,27 @@ class Hierarchy:
                        "disp1": [mk(s) for s in self.shapes for _ in range(3)],
                        "disp2": [mk(s) for s in self.shapes for _ in range(3)]}
         i1, i2 = MGInfo(), MGInfo()
-        st = self.lib.mg_lpt_pipeline(self.h, 1 if host else 0, _ptrs(deltas),
-                                      _ptrs(outputs["phi1"]), _ptrs(outputs["phi2"]),
-                                      _ptrs(outputs["disp1"]), _ptrs(outputs["disp2"]),
+        disp_shapes = [s for s in self.shapes for _ in range(3)]
+        st = self.lib.mg_lpt_pipeline(self.h, 1 if host else 0, _ptrs(deltas, self.shapes, host),
+                                      _ptrs(outputs["phi1"], self.shapes, host),
+                                      _ptrs(outputs["phi2"], self.shapes, host),
+                                      _ptrs(outputs["disp1"], disp_shapes, host),
+                                      _ptrs(outputs["disp2"], disp_shapes, host),
                                       ctypes.byref(i1), ctypes.byref(i2))
         self._check(st, "mg_lpt_pipeline", allow_noconv)
         return outputs, i1.as_dict(), i2.as_dict()
+
+    def set_profiling(self, families=()):
+        """Time every launch of the named kernel families with CUDA events."""
+        mask = 0
+        for name in families:
+            mask |= 1 << FAMILY_NAMES.index(name)
+        self._check(self.lib.mg_set_profiling(self.h, mask), "mg_set_profiling")
+
+    def stats(self, reset=False):
+        st = MGStats()
+        self._check(self.lib.mg_get_stats(self.h, ctypes.byref(st), 1 if reset else 0), "mg_get_stats")
+        return st.as_dict()
 
     def close(self):
         if getattr(self, "h", None):

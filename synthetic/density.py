@@ -41,7 +41,7 @@ def _kmag(shape, h):
 
 def _convolve_periodic(noise, h, power):
     amp = np.sqrt(power(_kmag(noise.shape, h)) / h ** 3)
-    return np.fft.ifftn(np.fft.fftn(noise) * amp).real
+    return np.ascontiguousarray(np.fft.ifftn(np.fft.fftn(noise) * amp).real)
 
 
 def _convolve_isolated(noise, h, power):
@@ -49,7 +49,7 @@ def _convolve_isolated(noise, h, power):
     padded = np.zeros(tuple(2 * n for n in shape))
     padded[:shape[0], :shape[1], :shape[2]] = noise
     out = _convolve_periodic(padded, h, power)
-    return out[:shape[0], :shape[1], :shape[2]]
+    return np.ascontiguousarray(out[:shape[0], :shape[1], :shape[2]])
 
 
 def _children_mean(a):

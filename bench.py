@@ -46,6 +46,10 @@ SMOOTH_OPS_PER_UPDATE = {2: 7, 4: 13, 6: 19}
 # in-place algorithmic bytes of one colour half-sweep per level-cell: read u of
 # both colours (8 B), f of the updated colour (4 B), write the updated colour (4 B)
 SMOOTH_BYTES_PER_CELL = 16.0
+# DRAM bytes (read + write) per updated cell of k_smooth_half<6,double> from one ncu
+# capture of the 128^3 launch (37.58 MB for 1,048,576 updates); scaled per launch by
+# the updated cells.  Set to None whenever the kernel changes.
+SMOOTH_TRAFFIC_PER_UPDATE = 37.58e6 / 1048576
 
 
 def workload():
@@ -320,7 +324,10 @@ def run_ours(args):
                        "rel_residual_2lpt": info2["rel_residual"]},
             "roofline": {"bound": "alu", "achieved": achieved_gops, "peak": FP64_PEAK_GOPS,
                          "unit": "G FP64 instr/s", "frac": achieved_gops / FP64_PEAK_GOPS,
-                         "traffic": None, "kernel": "k_smooth_half<6,double>",
+                         "traffic": (SMOOTH_TRAFFIC_PER_UPDATE * updates_per_launch
+                                     if SMOOTH_TRAFFIC_PER_UPDATE else None),
+                         "traffic_unit": "bytes per launch (ncu, scaled by updated cells)",
+                         "kernel": "k_smooth_half<6,double>",
                          "peak_source": "nominal FP64 1.25 TFLOP/s (recipe) = 625 G FMA/s",
                          "ms_per_launch": ms_per_launch, "updates_per_launch": updates_per_launch,
                          "hbm_view": {"achieved_gbs": smooth_gbs, "peak_gbs": 6765.0,

@@ -132,6 +132,23 @@ mg_status mg_lpt_pipeline(mg_hierarchy* h, int host_buffers, const double* const
                           double* const phi1[], double* const phi2[], double* const disp1[],
                           double* const disp2[], mg_info* info1, mg_info* info2);
 
+/* 2LPT source tau of one periodic grid, with no device allocation.  The paper
+ * has no counterpart; this is for callers that cannot allocate device memory
+ * when they need the result (their device memory is held by their own pool,
+ * they are given a stream but no allocator, or they must avoid the device
+ * synchronisation cudaMalloc/cudaFree can cause).
+ *   phi, tau  caller-owned device arrays, dense float64 [n0][n1][n2]
+ *   box       length of axis 0 (h = box / n0); order 2, 4 or 6
+ *   err       optional message buffer of len bytes
+ * Working memory is one static device array of 6 MiB (two ghost-padded grids,
+ * about 64^3 cells at order 6); larger grids return MG_EINVAL with a message.
+ * The first call on each device looks up the array's address and should be
+ * made outside stream capture.  Calls share the array: calls whose work
+ * overlaps on the GPU race.  Asynchronous on cuda_stream. */
+mg_status mg_lpt2_source_periodic_static(const double* phi, double* tau, int n0, int n1,
+                                         int n2, double box, int order, void* cuda_stream,
+                                         char* err, size_t len);
+
 /* Kernel families for launch counting and event timing. */
 typedef enum {
   MG_K_SMOOTH = 0,     /* red-black half-sweep                                 */

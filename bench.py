@@ -47,9 +47,9 @@ SMOOTH_OPS_PER_UPDATE = {2: 7, 4: 13, 6: 19}
 # both colours (8 B), f of the updated colour (4 B), write the updated colour (4 B)
 SMOOTH_BYTES_PER_CELL = 16.0
 # DRAM bytes (read + write) per updated cell of k_smooth_half<6,double> from one ncu
-# capture of the 128^3 launch (37.58 MB for 1,048,576 updates); scaled per launch by
+# capture of the 128^3 launch; scaled per launch by
 # the updated cells.  Set to None whenever the kernel changes.
-SMOOTH_TRAFFIC_PER_UPDATE = 37.58e6 / 1048576
+SMOOTH_TRAFFIC_PER_UPDATE = None
 
 
 def workload():

@@ -33,6 +33,9 @@ struct DevLevel {
   Int3 child_lo{0, 0, 0}, child_hi{0, 0, 0};  // region covered by the child, own cells
   double* u[2] = {nullptr, nullptr};
   int cur = 0;
+  // Periodic levels: every kernel that writes u also writes its ghost images,
+  // so ghosts are refilled only after u is loaded from outside.
+  bool ghosts_stale = true;
   double* f = nullptr;
   double* ffas = nullptr;
   double* ubar = nullptr;
@@ -244,7 +247,9 @@ mg_status tangential(mg_hierarchy* h, int l) {
 mg_status ghost_fill(mg_hierarchy* h, int l, bool edges) {
   DevLevel& L = h->L[l];
   if (L.periodic) {
-    KL(MG_K_GHOST, shell_of(L.G), launch_ghost_periodic<double>(L.G, L.u[L.cur], h->s));
+    if (L.ghosts_stale)
+      KL(MG_K_GHOST, shell_of(L.G), launch_ghost_periodic<double>(L.G, L.u[L.cur], h->s));
+    L.ghosts_stale = false;
     return MG_OK;
   }
   DevLevel& P = h->L[l - 1];
@@ -260,7 +265,7 @@ mg_status half_sweep(mg_hierarchy* h, int l, int colour) {
   ST(ghost_fill(h, l, false));
   const double a_f = L.geo.h * L.geo.h / centre_weight(h->cfg.order);
   KL(MG_K_SMOOTH, (cells_of(L.G) + 1) / 2, launch_smooth_half<double>(h->cfg.order, L.G, L.u[L.cur], L.u[1 - L.cur], L.ffas, a_f,
-                                colour, h->s));
+                                colour, L.periodic ? 1 : 0, h->s));
   L.cur ^= 1;
   return MG_OK;
 }
@@ -278,20 +283,20 @@ mg_status vcycle(mg_hierarchy* h, int l) {
   const int order = h->cfg.order;
   if (l == 0) {
     KL(MG_K_COARSEST, cells_of(L.G), launch_coarsest(L.G, L.ffas, L.u[L.cur], L.kern, h->s));
-    KL(MG_K_GHOST, shell_of(L.G), launch_ghost_periodic<double>(L.G, L.u[L.cur], h->s));
     return MG_OK;
   }
   DevLevel& P = h->L[l - 1];
   ST(smooth(h, l, h->cfg.nu1));
   ST(ghost_fill(h, l, false));
   KL(MG_K_RESTRICT, cells_of(L.G), launch_residual_restrict<double>(order, L.G, L.u[L.cur], L.ffas, 1.0 / (L.geo.h * L.geo.h),
-                                      P.G, P.u[P.cur], P.ffas, L.ubar, L.off, L.cn, h->s));
-  if (P.periodic) KL(MG_K_GHOST, shell_of(P.G), launch_ghost_periodic<double>(P.G, P.u[P.cur], h->s));
+                                      P.G, P.u[P.cur], P.ffas, L.ubar, L.off, L.cn,
+                                      P.periodic ? 1 : 0, h->s));
   KL(MG_K_FAS, cells_of(L.cn), launch_fas_source<double>(order, P.G, P.u[P.cur], P.ffas, 1.0 / (P.geo.h * P.geo.h), L.off,
                                L.cn, h->s));
   ST(vcycle(h, l - 1));
   if (!L.periodic) ST(tangential(h, l));
-  KL(MG_K_PROLONG, cells_of(L.G), launch_prolong<double>(L.G, L.u[L.cur], P.G, P.u[P.cur], L.ubar, L.off, L.cn, h->s));
+  KL(MG_K_PROLONG, cells_of(L.G), launch_prolong<double>(L.G, L.u[L.cur], P.G, P.u[P.cur], L.ubar, L.off, L.cn,
+                                 L.periodic ? 1 : 0, h->s));
   ST(smooth(h, l, h->cfg.nu2));
   return MG_OK;
 }
@@ -344,6 +349,7 @@ mg_status solve_prepared(mg_hierarchy* h, mg_info* info) {
     KL(MG_K_COPY, e, launch_fill(L.u[0], e, 0.0, h->s));
     KL(MG_K_COPY, e, launch_fill(L.u[1], e, 0.0, h->s));
     L.cur = 0;
+    L.ghosts_stale = false;
   }
   for (int l = h->base + 1; l <= finest(h); ++l) ST(tangential(h, l));
   mg_info local;
@@ -419,6 +425,7 @@ mg_status load_potential(mg_hierarchy* h, const double* const phi[], bool host) 
   for (int l = h->base; l <= finest(h); ++l) {
     DevLevel& L = h->L[l];
     ST(load_leaf(h, l, phi[l - h->base], L.u[L.cur], host));
+    L.ghosts_stale = true;
   }
   ST(sync_covered(h));
   for (int l = h->base + 1; l <= finest(h); ++l) ST(tangential(h, l));

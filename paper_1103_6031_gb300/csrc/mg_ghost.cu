@@ -126,95 +126,79 @@ __global__ void __launch_bounds__(128)
   }
 }
 
+// One thread per fine column of a face; the 4 columns under one parent face
+// element are 4 consecutive lanes (a "quad"), which share the parent flux and
+// the mean of their fine fluxes through warp shuffles.
 template <int ORDER, typename T>
 __global__ void __launch_bounds__(128)
     k_cf_flux(Grid F, T* __restrict__ u, FaceSet fs, CfWeights w, const T* __restrict__ inter,
               const T* __restrict__ fc_unc, T h, T invh, T invH, int flux_fix) {
   constexpr int half = ORDER / 2;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= fs.ebase[6]) return;
-  const int f = face_of(fs, t, fs.ebase);
+  if (t >= 4 * fs.ebase[6]) return;
+  const unsigned quad = __activemask();
+  const long long e = t >> 2;
+  const int col = (int)(t & 3);
+  const int f = face_of(fs, e, fs.ebase);
   const int a = f >> 1, side = f & 1;
-  int b, c;
-  face_axes(a, b, c);
   const int nt0 = fs.nt[f][0], nt1 = fs.nt[f][1];
-  const long long loc = t - fs.ebase[f];
+  const long long loc = e - fs.ebase[f];
   const int jc = (int)(loc / (nt1 / 2)), kc = (int)(loc % (nt1 / 2));
-  const int nf[3] = {F.n0, F.n1, F.n2};
-  const int na = nf[a];
-  int crd[3];
-  // parent flux: uncovered part (precomputed) + covered cells as mean of 8 children
-  T fc = fc_unc[t];
-  {
-    T cov = T(0);
+  const int tj = 2 * jc + (col >> 1), tk = 2 * kc + (col & 1);
+  const long long sx = (long long)F.Y * F.Zp, sy = F.Zp;
+  // strides along the normal (a) and the tangential axes (b, c) of this face
+  const long long sa = a == 0 ? sx : (a == 1 ? sy : 1);
+  const long long sb = a == 0 ? sy : sx;
+  const long long sc = a == 2 ? sy : 1;
+  const int na = a == 0 ? F.n0 : (a == 1 ? F.n1 : F.n2);
+  // element (0 along the normal, tj, tk); moving inwards is +sa (low face) or -sa (high)
+  const long long col0 = gidx(F, 0, 0, 0) + tj * sb + tk * sc;
+  const long long in0 = side == 0 ? col0 : col0 + (long long)(na - 1) * sa;
+  const long long step = side == 0 ? sa : -sa;
+  // fine interior values q = 0 .. half from the face
+  T v[half + 1];
 #pragma unroll
-    for (int d = 0; d < half; ++d) {
-      const int s = side == 0 ? half + d : half - 1 - d;
-      const int i0 = side == 0 ? 2 * d : na - 2 - 2 * d;
-      T sum = T(0);
+  for (int q = 0; q <= half; ++q) v[q] = u[in0 + q * step];
+  // parent flux: uncovered part + covered parent cells as the mean of their 8
+  // children; each column holds 2 of the 8 (normal 2d, 2d+1)
+  T cov = T(0);
 #pragma unroll
-      for (int di = 0; di < 2; ++di)
-#pragma unroll
-        for (int dj = 0; dj < 2; ++dj)
-#pragma unroll
-          for (int dk = 0; dk < 2; ++dk) {
-            crd[a] = i0 + di;
-            crd[b] = 2 * jc + dj;
-            crd[c] = 2 * kc + dk;
-            sum += u[gidx(F, crd[0], crd[1], crd[2])];
-          }
-      cov = fma(T(w.flux[s]), sum * T(0.125), cov);
-    }
-    fc = fma(cov, invH, fc);
+  for (int d = 0; d < half; ++d) {
+    const int s = side == 0 ? half + d : half - 1 - d;
+    T pair = u[in0 + (2 * d) * step] + u[in0 + (2 * d + 1) * step];
+    pair += __shfl_xor_sync(quad, pair, 1);
+    pair += __shfl_xor_sync(quad, pair, 2);
+    cov = fma(T(w.flux[s]), pair * T(0.125), cov);
   }
-  T ghost[4][half];
-  T ffsum = T(0);
+  const T fc = fma(cov, invH, fc_unc[e]);
+  T cq[half];
 #pragma unroll
-  for (int col = 0; col < 4; ++col) {
-    const int tj = 2 * jc + (col >> 1), tk = 2 * kc + (col & 1);
-    crd[b] = tj;
-    crd[c] = tk;
-    T v[half + 1];
+  for (int q = 0; q < half; ++q) cq[q] = inter[fs.base[f] + ((long long)q * nt0 + tj) * nt1 + tk];
+  T ghost[half];
 #pragma unroll
-    for (int q = 0; q <= half; ++q) {
-      crd[a] = side == 0 ? q : na - 1 - q;
-      v[q] = u[gidx(F, crd[0], crd[1], crd[2])];
-    }
-    T cq[half];
+  for (int m = 0; m < half; ++m) {
+    T gv = T(0);
 #pragma unroll
-    for (int q = 0; q < half; ++q)
-      cq[q] = inter[fs.base[f] + ((long long)q * nt0 + tj) * nt1 + tk];
+    for (int q = 0; q < half; ++q) gv = fma(T(w.ncoarse[m][q]), cq[q], gv);
 #pragma unroll
-    for (int m = 0; m < half; ++m) {
-      T gv = T(0);
-#pragma unroll
-      for (int q = 0; q < half; ++q) gv = fma(T(w.ncoarse[m][q]), cq[q], gv);
-#pragma unroll
-      for (int q = 0; q <= half; ++q) gv = fma(T(w.nfine[m][q]), v[q], gv);
-      ghost[col][m] = gv;
-    }
-    T ff = T(0);
-#pragma unroll
-    for (int s = 0; s < ORDER; ++s) {
-      T x;
-      if (side == 0) x = s < half ? ghost[col][half - 1 - s] : v[s - half];
-      else x = s < half ? v[half - 1 - s] : ghost[col][s - half];
-      ff = fma(T(w.flux[s]), x, ff);
-    }
-    ffsum += ff * invh;
+    for (int q = 0; q <= half; ++q) gv = fma(T(w.nfine[m][q]), v[q], gv);
+    ghost[m] = gv;
   }
+  T ff = T(0);
+#pragma unroll
+  for (int s = 0; s < ORDER; ++s) {
+    T x;
+    if (side == 0) x = s < half ? ghost[half - 1 - s] : v[s - half];
+    else x = s < half ? v[half - 1 - s] : ghost[s - half];
+    ff = fma(T(w.flux[s]), x, ff);
+  }
+  ff *= invh;
+  ff += __shfl_xor_sync(quad, ff, 1);
+  ff += __shfl_xor_sync(quad, ff, 2);
   T shift = T(0);
-  if (flux_fix) shift = (fc - T(0.25) * ffsum) * h / T(w.ghost_coef[side]);
+  if (flux_fix) shift = (fc - T(0.25) * ff) * h / T(w.ghost_coef[side]);
 #pragma unroll
-  for (int col = 0; col < 4; ++col) {
-    crd[b] = 2 * jc + (col >> 1);
-    crd[c] = 2 * kc + (col & 1);
-#pragma unroll
-    for (int m = 0; m < half; ++m) {
-      crd[a] = side == 0 ? -1 - m : na + m;
-      u[gidx(F, crd[0], crd[1], crd[2])] = ghost[col][m] + shift;
-    }
-  }
+  for (int m = 0; m < half; ++m) u[in0 - (m + 1) * step] = ghost[m] + shift;
 }
 
 template <int ORDER, typename T>
@@ -281,7 +265,7 @@ cudaError_t launch_cf_flux(int order, const Grid& F, T* u, const FaceSet& fs, co
                            const T* inter, const T* fc_unc, double h, double invh, double invH,
                            int flux_fix, cudaStream_t s) {
   const int block = 128;
-  const unsigned grid = (unsigned)((fs.ebase[6] + block - 1) / block);
+  const unsigned grid = (unsigned)((4 * fs.ebase[6] + block - 1) / block);
   switch (order) {
     case 2: k_cf_flux<2, T><<<grid, block, 0, s>>>(F, u, fs, w, inter, fc_unc, T(h), T(invh), T(invH), flux_fix); break;
     case 4: k_cf_flux<4, T><<<grid, block, 0, s>>>(F, u, fs, w, inter, fc_unc, T(h), T(invh), T(invH), flux_fix); break;

@@ -58,17 +58,17 @@ void make_faceset(const Grid& F, int half, FaceSet* fs);
 // ---- kernels: smoothing and inter-level transfer (mg_smooth.cu) ----
 template <typename T>
 cudaError_t launch_smooth_half(int order, const Grid& G, const T* uin, T* uout, const T* f,
-                               double a_f, int colour, cudaStream_t s);
+                               double a_f, int colour, int periodic, cudaStream_t s);
 template <typename T>
 cudaError_t launch_residual_restrict(int order, const Grid& F, const T* u, const T* f,
                                      double invh2, const Grid& P, T* pu, T* pfas, T* ubar,
-                                     Int3 off, Int3 cn, cudaStream_t s);
+                                     Int3 off, Int3 cn, int parent_periodic, cudaStream_t s);
 template <typename T>
 cudaError_t launch_fas_source(int order, const Grid& P, const T* pu, T* pfas, double invH2,
                               Int3 off, Int3 cn, cudaStream_t s);
 template <typename T>
 cudaError_t launch_prolong(const Grid& F, T* u, const Grid& P, const T* pu, const T* ubar,
-                           Int3 off, Int3 cn, cudaStream_t s);
+                           Int3 off, Int3 cn, int periodic, cudaStream_t s);
 template <typename T>
 cudaError_t launch_restrict_u(const Grid& F, const T* u, const Grid& P, T* pu, Int3 off,
                               Int3 cn, cudaStream_t s);

@@ -39,27 +39,38 @@ __device__ __forceinline__ double lap_w(int s) {
 
 // Periodic pseudo-inverse of L on the coarsest level as a circular convolution:
 // u(x) = sum_y K(x - y) f(y), K precomputed on the host from the DFT symbol.
-__global__ void __launch_bounds__(128)
+// One block per output cell; the block's threads split the sum over y.  The
+// result is also written to the cell's periodic ghost images.
+constexpr int kCoarseBlock = 128;
+
+__global__ void __launch_bounds__(kCoarseBlock)
     k_coarsest(Grid G, const double* __restrict__ f, double* __restrict__ u,
                const double* __restrict__ kern) {
-  const int n = G.n0 * G.n1 * G.n2;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= n) return;
-  const int xk = x % G.n2, xj = (x / G.n2) % G.n1, xi = x / (G.n1 * G.n2);
+  const int n12 = G.n1 * G.n2;
+  const int n = G.n0 * n12;
+  const int x = blockIdx.x;
+  const int xk = x % G.n2, xj = (x / G.n2) % G.n1, xi = x / n12;
   double acc = 0.0;
-  for (int yi = 0; yi < G.n0; ++yi) {
-    const int di = (xi - yi + G.n0) % G.n0;
-    for (int yj = 0; yj < G.n1; ++yj) {
-      const int dj = (xj - yj + G.n1) % G.n1;
-      const double* krow = kern + ((long long)di * G.n1 + dj) * G.n2;
-      const double* frow = f + gidx(G, yi, yj, 0);
-      for (int yk = 0; yk < G.n2; ++yk) {
-        const int dk = (xk - yk + G.n2) % G.n2;
-        acc = fma(__ldg(krow + dk), __ldg(frow + yk), acc);
-      }
-    }
+  for (int y = threadIdx.x; y < n; y += kCoarseBlock) {
+    const int yk = y % G.n2, yj = (y / G.n2) % G.n1, yi = y / n12;
+    int di = xi - yi, dj = xj - yj, dk = xk - yk;
+    di += di < 0 ? G.n0 : 0;
+    dj += dj < 0 ? G.n1 : 0;
+    dk += dk < 0 ? G.n2 : 0;
+    acc = fma(__ldg(kern + (di * G.n1 + dj) * G.n2 + dk), __ldg(f + gidx(G, yi, yj, yk)), acc);
   }
-  u[gidx(G, xi, xj, xk)] = acc;
+  __shared__ double red[kCoarseBlock];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+#pragma unroll
+  for (int w = kCoarseBlock / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    u[gidx(G, xi, xj, xk)] = red[0];
+    write_images<double>(G, u, xi, xj, xk, red[0]);
+  }
 }
 
 template <int BLOCK>
@@ -82,49 +93,57 @@ __device__ __forceinline__ void block_sum2(double& a, double& b) {
 
 constexpr int kRedBlock = 256;
 
-__device__ __forceinline__ bool covered(int i, int j, int k, Int3 lo, Int3 hi) {
-  return i >= lo.x && i < hi.x && j >= lo.y && j < hi.y && k >= lo.z && k < hi.z;
-}
-
+// One block per (x plane, 8 y rows); 32 lanes stride along z.  Block b writes
+// its partial sums to slot b, so the reduction order is fixed.
 template <int ORDER>
 __global__ void __launch_bounds__(kRedBlock)
     k_norm_partial(Grid G, const double* __restrict__ u, const double* __restrict__ f,
                    double invh2, double vol, Int3 clo, Int3 chi, double* __restrict__ partial) {
-  const long long n = (long long)G.n0 * G.n1 * G.n2;
   const long long sy = G.Zp, sx = (long long)G.Y * G.Zp;
+  const int i = blockIdx.y;
+  const int j = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   double rr = 0.0, ff = 0.0;
-  for (long long t = blockIdx.x * (long long)kRedBlock + threadIdx.x; t < n;
-       t += (long long)gridDim.x * kRedBlock) {
-    const int k = (int)(t % G.n2), j = (int)((t / G.n2) % G.n1), i = (int)(t / ((long long)G.n2 * G.n1));
-    if (covered(i, j, k, clo, chi)) continue;
-    const long long p = gidx(G, i, j, k);
-    const double fv = __ldg(f + p);
-    const double r = fma(-invh2, lap_h2<ORDER, double>(u, p, sy, sx), fv);
-    rr = fma(r, r, rr);
-    ff = fma(fv, fv, ff);
+  if (j < G.n1) {
+    const bool row_cov = i >= clo.x && i < chi.x && j >= clo.y && j < chi.y;
+    const long long row = gidx(G, i, j, 0);
+    for (int k = lane; k < G.n2; k += 32) {
+      if (row_cov && k >= clo.z && k < chi.z) continue;
+      const long long p = row + k;
+      const double fv = __ldg(f + p);
+      const double r = fma(-invh2, lap_h2<ORDER, double>(u, p, sy, sx), fv);
+      rr = fma(r, r, rr);
+      ff = fma(fv, fv, ff);
+    }
   }
   block_sum2<kRedBlock>(rr, ff);
   if (threadIdx.x == 0) {
-    partial[2 * blockIdx.x] = rr * vol;
-    partial[2 * blockIdx.x + 1] = ff * vol;
+    const int b = blockIdx.y * gridDim.x + blockIdx.x;
+    partial[2 * b] = rr * vol;
+    partial[2 * b + 1] = ff * vol;
   }
 }
 
 __global__ void __launch_bounds__(kRedBlock)
     k_sum_partial(Grid G, const double* __restrict__ f, double vol, Int3 clo, Int3 chi,
                   double* __restrict__ partial) {
-  const long long n = (long long)G.n0 * G.n1 * G.n2;
+  const int i = blockIdx.y;
+  const int j = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   double s = 0.0, unused = 0.0;
-  for (long long t = blockIdx.x * (long long)kRedBlock + threadIdx.x; t < n;
-       t += (long long)gridDim.x * kRedBlock) {
-    const int k = (int)(t % G.n2), j = (int)((t / G.n2) % G.n1), i = (int)(t / ((long long)G.n2 * G.n1));
-    if (covered(i, j, k, clo, chi)) continue;
-    s += __ldg(f + gidx(G, i, j, k));
+  if (j < G.n1) {
+    const bool row_cov = i >= clo.x && i < chi.x && j >= clo.y && j < chi.y;
+    const long long row = gidx(G, i, j, 0);
+    for (int k = lane; k < G.n2; k += 32) {
+      if (row_cov && k >= clo.z && k < chi.z) continue;
+      s += __ldg(f + row + k);
+    }
   }
   block_sum2<kRedBlock>(s, unused);
   if (threadIdx.x == 0) {
-    partial[2 * blockIdx.x] = s * vol;
-    partial[2 * blockIdx.x + 1] = 0.0;
+    const int b = blockIdx.y * gridDim.x + blockIdx.x;
+    partial[2 * b] = s * vol;
+    partial[2 * b + 1] = 0.0;
   }
 }
 
@@ -250,27 +269,24 @@ inline unsigned blocks_for(long long n, int b) { return (unsigned)((n + b - 1) /
 
 }  // namespace
 
-int norm_blocks(const Grid& G) {
-  const long long n = (long long)G.n0 * G.n1 * G.n2;
-  long long b = (n + kRedBlock - 1) / kRedBlock;
-  if (b > 1216) b = 1216;  // 8 x 152 SMs
-  return (int)b;
-}
+int norm_blocks(const Grid& G) { return ((G.n1 + 7) / 8) * G.n0; }
 
 cudaError_t launch_coarsest(const Grid& G, const double* f, double* u, const double* kern,
                             cudaStream_t s) {
   const int n = G.n0 * G.n1 * G.n2;
-  k_coarsest<<<blocks_for(n, 128), 128, 0, s>>>(G, f, u, kern);
+  k_coarsest<<<n, kCoarseBlock, 0, s>>>(G, f, u, kern);
   return cudaGetLastError();
 }
 
 cudaError_t launch_norm_partial(int order, const Grid& G, const double* u, const double* f,
                                 double invh2, double vol, Int3 clo, Int3 chi, double* partial,
                                 int blocks, cudaStream_t s) {
+  const dim3 grid((G.n1 + 7) / 8, G.n0);
+  if ((int)(grid.x * grid.y) != blocks) return cudaErrorInvalidValue;
   switch (order) {
-    case 2: k_norm_partial<2><<<blocks, kRedBlock, 0, s>>>(G, u, f, invh2, vol, clo, chi, partial); break;
-    case 4: k_norm_partial<4><<<blocks, kRedBlock, 0, s>>>(G, u, f, invh2, vol, clo, chi, partial); break;
-    case 6: k_norm_partial<6><<<blocks, kRedBlock, 0, s>>>(G, u, f, invh2, vol, clo, chi, partial); break;
+    case 2: k_norm_partial<2><<<grid, kRedBlock, 0, s>>>(G, u, f, invh2, vol, clo, chi, partial); break;
+    case 4: k_norm_partial<4><<<grid, kRedBlock, 0, s>>>(G, u, f, invh2, vol, clo, chi, partial); break;
+    case 6: k_norm_partial<6><<<grid, kRedBlock, 0, s>>>(G, u, f, invh2, vol, clo, chi, partial); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -278,7 +294,9 @@ cudaError_t launch_norm_partial(int order, const Grid& G, const double* u, const
 
 cudaError_t launch_sum_partial(const Grid& G, const double* f, double vol, Int3 clo, Int3 chi,
                                double* partial, int blocks, cudaStream_t s) {
-  k_sum_partial<<<blocks, kRedBlock, 0, s>>>(G, f, vol, clo, chi, partial);
+  const dim3 grid((G.n1 + 7) / 8, G.n0);
+  if ((int)(grid.x * grid.y) != blocks) return cudaErrorInvalidValue;
+  k_sum_partial<<<grid, kRedBlock, 0, s>>>(G, f, vol, clo, chi, partial);
   return cudaGetLastError();
 }
 

@@ -21,7 +21,7 @@ constexpr int kRowsY = 4;   // y rows per block
 template <int ORDER, typename T>
 __global__ void __launch_bounds__(kPairX* kRowsY)
     k_smooth_half(Grid G, const T* __restrict__ uin, T* __restrict__ uout,
-                  const T* __restrict__ f, T a_f, int colour) {
+                  const T* __restrict__ f, T a_f, int colour, int periodic) {
   const int t = blockIdx.x * kPairX + threadIdx.x;
   const int j = blockIdx.y * kRowsY + threadIdx.y;
   const int i = blockIdx.z;
@@ -33,7 +33,9 @@ __global__ void __launch_bounds__(kPairX* kRowsY)
   const int upd = (((i + j + k0) & 1) == colour) ? 0 : 1;
   const bool pair = (k0 + 1) < G.n2;
   if (!pair && upd == 1) {
-    uout[p0] = __ldg(uin + p0);
+    const T c = __ldg(uin + p0);
+    uout[p0] = c;
+    if (periodic) write_images<T>(G, uout, i, j, k0, c);
     return;
   }
   const long long p = p0 + upd;
@@ -56,8 +58,13 @@ __global__ void __launch_bounds__(kPairX* kRowsY)
       out.y = v;
     }
     *reinterpret_cast<V2*>(uout + p0) = out;
+    if (periodic) {
+      write_images<T>(G, uout, i, j, k0, out.x);
+      write_images<T>(G, uout, i, j, k0 + 1, out.y);
+    }
   } else {
     uout[p0] = v;
+    if (periodic) write_images<T>(G, uout, i, j, k0, v);
   }
 }
 
@@ -67,7 +74,7 @@ template <int ORDER, typename T>
 __global__ void __launch_bounds__(128)
     k_residual_restrict(Grid F, const T* __restrict__ u, const T* __restrict__ f, T invh2, Grid P,
                         T* __restrict__ pu, T* __restrict__ pfas, T* __restrict__ ubar, Int3 off,
-                        Int3 cn) {
+                        Int3 cn, int parent_periodic) {
   const int kc = blockIdx.x * blockDim.x + threadIdx.x;
   const int jc = blockIdx.y * blockDim.y + threadIdx.y;
   const int ic = blockIdx.z;
@@ -91,6 +98,7 @@ __global__ void __launch_bounds__(128)
   const long long q = gidx(P, off.x + ic, off.y + jc, off.z + kc);
   const T mu = su * T(0.125);
   pu[q] = mu;
+  if (parent_periodic) write_images<T>(P, pu, off.x + ic, off.y + jc, off.z + kc, mu);
   pfas[q] = sr * T(0.125);
   ubar[((long long)ic * cn.y + jc) * cn.z + kc] = mu;
 }
@@ -114,7 +122,7 @@ __global__ void __launch_bounds__(128)
 template <typename T>
 __global__ void __launch_bounds__(128)
     k_prolong(Grid F, T* __restrict__ u, Grid P, const T* __restrict__ pu,
-              const T* __restrict__ ubar, Int3 off, Int3 cn) {
+              const T* __restrict__ ubar, Int3 off, Int3 cn, int periodic) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int i = blockIdx.z;
@@ -129,6 +137,10 @@ __global__ void __launch_bounds__(128)
   v.x += d;
   v.y += d;
   *reinterpret_cast<V2*>(u + p) = v;
+  if (periodic) {
+    write_images<T>(F, u, i, j, k0, v.x);
+    write_images<T>(F, u, i, j, k0 + 1, v.y);
+  }
 }
 
 // parent u := mean of children (covered region), one thread per parent cell.
@@ -159,14 +171,14 @@ dim3 coarse_grid(Int3 cn, dim3 block) {
 
 template <typename T>
 cudaError_t launch_smooth_half(int order, const Grid& G, const T* uin, T* uout, const T* f,
-                               double a_f, int colour, cudaStream_t s) {
+                               double a_f, int colour, int periodic, cudaStream_t s) {
   const int pairs = (G.n2 + 1) / 2;
   dim3 block(kPairX, kRowsY, 1);
   dim3 grid((pairs + kPairX - 1) / kPairX, (G.n1 + kRowsY - 1) / kRowsY, G.n0);
   switch (order) {
-    case 2: k_smooth_half<2, T><<<grid, block, 0, s>>>(G, uin, uout, f, T(a_f), colour); break;
-    case 4: k_smooth_half<4, T><<<grid, block, 0, s>>>(G, uin, uout, f, T(a_f), colour); break;
-    case 6: k_smooth_half<6, T><<<grid, block, 0, s>>>(G, uin, uout, f, T(a_f), colour); break;
+    case 2: k_smooth_half<2, T><<<grid, block, 0, s>>>(G, uin, uout, f, T(a_f), colour, periodic); break;
+    case 4: k_smooth_half<4, T><<<grid, block, 0, s>>>(G, uin, uout, f, T(a_f), colour, periodic); break;
+    case 6: k_smooth_half<6, T><<<grid, block, 0, s>>>(G, uin, uout, f, T(a_f), colour, periodic); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -175,13 +187,13 @@ cudaError_t launch_smooth_half(int order, const Grid& G, const T* uin, T* uout, 
 template <typename T>
 cudaError_t launch_residual_restrict(int order, const Grid& F, const T* u, const T* f,
                                      double invh2, const Grid& P, T* pu, T* pfas, T* ubar,
-                                     Int3 off, Int3 cn, cudaStream_t s) {
+                                     Int3 off, Int3 cn, int parent_periodic, cudaStream_t s) {
   dim3 block(32, 4, 1);
   dim3 grid = coarse_grid(cn, block);
   switch (order) {
-    case 2: k_residual_restrict<2, T><<<grid, block, 0, s>>>(F, u, f, T(invh2), P, pu, pfas, ubar, off, cn); break;
-    case 4: k_residual_restrict<4, T><<<grid, block, 0, s>>>(F, u, f, T(invh2), P, pu, pfas, ubar, off, cn); break;
-    case 6: k_residual_restrict<6, T><<<grid, block, 0, s>>>(F, u, f, T(invh2), P, pu, pfas, ubar, off, cn); break;
+    case 2: k_residual_restrict<2, T><<<grid, block, 0, s>>>(F, u, f, T(invh2), P, pu, pfas, ubar, off, cn, parent_periodic); break;
+    case 4: k_residual_restrict<4, T><<<grid, block, 0, s>>>(F, u, f, T(invh2), P, pu, pfas, ubar, off, cn, parent_periodic); break;
+    case 6: k_residual_restrict<6, T><<<grid, block, 0, s>>>(F, u, f, T(invh2), P, pu, pfas, ubar, off, cn, parent_periodic); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -203,11 +215,11 @@ cudaError_t launch_fas_source(int order, const Grid& P, const T* pu, T* pfas, do
 
 template <typename T>
 cudaError_t launch_prolong(const Grid& F, T* u, const Grid& P, const T* pu, const T* ubar,
-                           Int3 off, Int3 cn, cudaStream_t s) {
+                           Int3 off, Int3 cn, int periodic, cudaStream_t s) {
   dim3 block(32, 4, 1);
   const int pairs = F.n2 / 2;
   dim3 grid((pairs + 31) / 32, (F.n1 + 3) / 4, F.n0);
-  k_prolong<T><<<grid, block, 0, s>>>(F, u, P, pu, ubar, off, cn);
+  k_prolong<T><<<grid, block, 0, s>>>(F, u, P, pu, ubar, off, cn, periodic);
   return cudaGetLastError();
 }
 
@@ -222,14 +234,14 @@ cudaError_t launch_restrict_u(const Grid& F, const T* u, const Grid& P, T* pu, I
 
 #define MGK_INSTANTIATE(T)                                                                     \
   template cudaError_t launch_smooth_half<T>(int, const Grid&, const T*, T*, const T*, double, \
-                                             int, cudaStream_t);                               \
+                                             int, int, cudaStream_t);                          \
   template cudaError_t launch_residual_restrict<T>(int, const Grid&, const T*, const T*,       \
                                                    double, const Grid&, T*, T*, T*, Int3,      \
-                                                   Int3, cudaStream_t);                        \
+                                                   Int3, int, cudaStream_t);                   \
   template cudaError_t launch_fas_source<T>(int, const Grid&, const T*, T*, double, Int3,      \
                                             Int3, cudaStream_t);                               \
   template cudaError_t launch_prolong<T>(const Grid&, T*, const Grid&, const T*, const T*,     \
-                                         Int3, Int3, cudaStream_t);                            \
+                                         Int3, Int3, int, cudaStream_t);                       \
   template cudaError_t launch_restrict_u<T>(const Grid&, const T*, const Grid&, T*, Int3,      \
                                             Int3, cudaStream_t);
 

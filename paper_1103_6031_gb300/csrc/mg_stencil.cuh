@@ -55,6 +55,34 @@ __device__ __forceinline__ T lap_h2(const T* __restrict__ u, long long p, long l
   return acc;
 }
 
+// On a periodic level, every ghost cell is the image of one interior cell (all
+// sides are >= g).  Writes v to the images of interior cell (i, j, k); the cell
+// itself is written by the caller.
+template <typename T>
+__device__ __forceinline__ void write_images(const Grid& G, T* __restrict__ u, int i, int j,
+                                             int k, T v) {
+  const int g = G.g;
+  if (i >= g && i < G.n0 - g && j >= g && j < G.n1 - g && k >= g && k < G.n2 - g) return;
+  int is[2], js[2], ks[2];
+  int ni = 0, nj = 0, nk = 0;
+  if (i < g) is[ni++] = i + G.n0;
+  if (i >= G.n0 - g) is[ni++] = i - G.n0;
+  if (j < g) js[nj++] = j + G.n1;
+  if (j >= G.n1 - g) js[nj++] = j - G.n1;
+  if (k < g) ks[nk++] = k + G.n2;
+  if (k >= G.n2 - g) ks[nk++] = k - G.n2;
+  // all combinations of (own or image) per axis, except own on every axis
+  for (int a = 0; a <= ni; ++a)
+    for (int b = 0; b <= nj; ++b)
+      for (int c = 0; c <= nk; ++c) {
+        if (a == 0 && b == 0 && c == 0) continue;
+        const int ii = a == 0 ? i : is[a - 1];
+        const int jj = b == 0 ? j : js[b - 1];
+        const int kk = c == 0 ? k : ks[c - 1];
+        u[gidx(G, ii, jj, kk)] = v;
+      }
+}
+
 template <typename T>
 struct Vec2;
 template <>

@@ -34,6 +34,8 @@ METRIC = "level-cells solved/s to 1e-6 rel. error; % HBM peak; p50/p99 solve lat
 UNIT = "level-cells/s"
 SOLVE_TOL = 1e-7
 SEED = 2
+# float32 V-cycles per float64 refinement step in the mixed-precision variant
+MIXED_INNER_CYCLES = 4
 # V-cycles of one full step at SOLVE_TOL on this workload (1LPT + 2LPT), as the
 # GPU arm reports them; the oracle arm scales its one-cycle sample by this.
 CYCLES_PER_STEP = 14
@@ -231,7 +233,11 @@ def run_ours(args):
 
     geom = workload()
     deltas_np = make_delta(geom, SEED)
-    cfg = pkg.config_from_geometry(geom, tol=SOLVE_TOL, max_cycles=50)
+    if args.profile_run and args.precision == "mixed":
+        cfg = pkg.config_from_geometry(geom, tol=SOLVE_TOL, max_cycles=50, precision=pkg.MG_MIXED,
+                                       inner_cycles=MIXED_INNER_CYCLES)
+    else:
+        cfg = pkg.config_from_geometry(geom, tol=SOLVE_TOL, max_cycles=50)
     h = pkg.Hierarchy(cfg)
     stream = h.stream
     deltas = [torch.from_numpy(x).to(device) for x in deltas_np]
@@ -280,6 +286,43 @@ def run_ours(args):
     achieved_gops = ops / (ms_per_launch * 1e-3) / 1e9
     smooth_gbs = SMOOTH_BYTES_PER_CELL * 2 * updates_per_launch / (ms_per_launch * 1e-3) / 1e9
     total_smooth_ms = sm["event_ms"]
+
+    # mixed precision on the same workload and stopping rule (float32 V-cycles
+    # inside float64 iterative refinement), device-resident like the headline
+    mixed = None
+    if not args.profile_run:
+        cfg_m = pkg.config_from_geometry(geom, tol=SOLVE_TOL, max_cycles=50,
+                                         precision=pkg.MG_MIXED, inner_cycles=MIXED_INNER_CYCLES)
+        hm = pkg.Hierarchy(cfg_m)
+        for w in range(args.warmup):
+            _, m1, m2 = hm.pipeline(deltas, out)
+        hm.stats(reset=True)
+        barrier()
+        evm = []
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            _, m1, m2 = hm.pipeline(deltas, out)
+            b.record(stream)
+            evm.append((a, b))
+        barrier()
+        mixed_ms = [a.elapsed_time(b) for a, b in evm]
+        mstats = hm.stats(reset=True)
+        mixed_value, mixed_ms_step = aggregate(sum(mixed_ms), geom.level_cells() * args.steps,
+                                               args.steps, dist, device)
+        mixed = {"value": mixed_value, "unit": UNIT, "ms_per_step": mixed_ms_step,
+                 "latency_ms": {"p50": statistics.median(mixed_ms),
+                                "p99": sorted(mixed_ms)[max(0, int(round(0.99 * len(mixed_ms))) - 1)]},
+                 "precision": "float32 V-cycles (smoothing, transfers, coarse-fine ghosts) inside "
+                              "float64 refinement (residual, coarsest solve, update)",
+                 "inner_cycles": MIXED_INNER_CYCLES,
+                 "outer": {"1lpt": m1["cycles"], "2lpt": m2["cycles"]},
+                 "rel_residual": {"1lpt": m1["rel_residual"], "2lpt": m2["rel_residual"]},
+                 "gpu_launches": sum(v["launches"] for v in mstats.values()),
+                 "error_bound": "<= 1e-6 RMS relative vs float64 (tests/test_gpu_parity.py)"}
+        hm.close()
 
     if args.profile_run:
         if rank == 0:
@@ -336,6 +379,7 @@ def run_ours(args):
                          "share_of_step": total_smooth_ms / max(sum(step_ms), 1e-9)},
             "gpu_launches": launches,
             "clocks": clocks,
+            "mixed_precision": mixed,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h,
                     "ms_per_step": statistics.mean(e2e_ms)},
@@ -359,6 +403,8 @@ def main(argv=None):
                     help="leave out the CPU-oracle baseline")
     ap.add_argument("--profile-run", action="store_true",
                     help="timed steps only: no end-to-end pass, no CPU baseline (for ncu)")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
+                    help="precision of the timed steps of a --profile-run")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)

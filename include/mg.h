@@ -26,9 +26,12 @@
  * Ownership: inputs and outputs are caller-owned; device pointers unless a
  * call says otherwise.  The hierarchy owns its padded working state, allocated
  * through cfg->dev_alloc/dev_free (cudaMalloc/cudaFree when both are NULL) and
- * released by mg_hierarchy_destroy.  Calls are ordered on the hierarchy's
- * stream; the solve calls read one 16-byte convergence record back per V-cycle
- * (so they return with the stream synchronised).
+ * released by mg_hierarchy_destroy.  Each call is ordered after the work
+ * already queued on the caller's stream (given at create time) and the
+ * caller's stream is ordered after the call's work; internally the hierarchy
+ * runs on its own non-blocking stream so that its cycles can be captured and
+ * replayed as CUDA graphs.  The solve calls read one 32-byte convergence record
+ * back per V-cycle (so they return with the work finished).
  *
  * Errors: every call returns an mg_status; no exception or abort crosses the
  * ABI.  mg_last_error() gives a message for the last failing call on a handle.
@@ -56,7 +59,16 @@ typedef enum {
   MG_ETIMEOUT = 5  /* reserved: bounded device-side wait expired               */
 } mg_status;
 
+/* MG_FP64: every step in float64.  MG_MIXED: iterative refinement; the
+ * residual f - L u, the coarsest-level solve and the update u += e are float64,
+ * the correction equation L e = r is solved by inner_cycles float32 V-cycles
+ * (smoothing, transfers and coarse-fine ghosts in float32) per outer iteration;
+ * the stopping test is the same float64 leaf residual norm. */
 typedef enum { MG_FP64 = 0, MG_MIXED = 1 } mg_precision;
+
+/* MG_FLAG_NO_GRAPHS: launch every kernel on the stream instead of replaying one
+ * captured CUDA graph per V-cycle (MG_FP64) or per outer iteration (MG_MIXED). */
+#define MG_FLAG_NO_GRAPHS 1
 
 typedef struct {
   int n_levels;                        /* 1 = base only; 1 + number of nests            */
@@ -67,7 +79,10 @@ typedef struct {
   int order;                           /* FD order: 2, 4 or 6                           */
   int precision;                       /* mg_precision                                  */
   int nu1, nu2;                        /* pre/post smoothing sweeps (paper: 2, 2)       */
-  int max_cycles;                      /* V-cycle limit per solve                       */
+  int max_cycles;                      /* V-cycle limit per solve (MG_MIXED: outer     */
+                                       /* refinement iterations)                        */
+  int inner_cycles;                    /* MG_MIXED: float32 V-cycles per outer iteration */
+  int flags;                           /* MG_FLAG_* bits; 0 = defaults                  */
   double tol;                          /* stop when leaf |r| / leaf |f| <= tol          */
   void* (*dev_alloc)(size_t bytes, void* ctx);
   void (*dev_free)(void* ptr, void* ctx);
@@ -75,14 +90,15 @@ typedef struct {
 } mg_config;
 
 typedef struct {
-  int cycles;                          /* V-cycles run                                  */
+  int cycles;                          /* V-cycles run (MG_MIXED: outer iterations)     */
   double rel_residual;                 /* final leaf |r| / leaf |f|                     */
   double source_mean;                  /* composite mean removed from the source        */
   double history[MG_MAX_HISTORY];      /* rel_residual after each cycle                 */
+  int inner_cycles;                    /* MG_MIXED: float32 V-cycles run in total       */
 } mg_info;
 
 /* Fill *cfg with defaults: order 2, FP64, nu1 = nu2 = 2, max_cycles 50,
- * tol 1e-10, box 1, no nests, NULL allocator.  Host only. */
+ * inner_cycles 2, tol 1e-10, box 1, no nests, NULL allocator.  Host only. */
 void mg_config_default(mg_config* cfg);
 
 /* Check the geometry and parameters without touching a GPU.  On failure
@@ -170,9 +186,11 @@ typedef struct {
   long long timed[MG_K_FAMILIES];     /* launches that carried events                     */
 } mg_stats;
 
-/* Time every launch of the families in mask (bit f = family f) with a CUDA
- * event pair on the hierarchy's stream (0 disables).  Adds two event records
- * per timed launch. */
+/* Time launches of the families in mask (bit f = family f) with CUDA event
+ * pairs on the hierarchy's stream (0 disables): every launch outside the
+ * V-cycle loops, and inside the loops the launches of the first cycle (or
+ * outer iteration) of each solve, a sample that visits every level once.
+ * mg_stats.timed counts the timed launches. */
 mg_status mg_set_profiling(mg_hierarchy* h, unsigned mask);
 
 /* Copy the counters out (synchronising the stream to read event times) and,

@@ -6,6 +6,14 @@
 // the parent through coarse-fine interpolation with flux matching.  Every step
 // is a kernel launch on the hierarchy's stream; the host only sequences them
 // and reads back one convergence record per cycle.
+//
+// Precision.  MG_FP64 runs the V-cycle on float64 buffers.  MG_MIXED keeps a
+// float64 solution on the leaf levels only; each outer iteration computes the
+// float64 composite residual r = f - L u (which also gives the convergence
+// norm), solves L e = r from e = 0 with float32 V-cycles on float32 buffers of
+// every level (the same kernels instantiated for float; coarse-fine ghosts,
+// flux matching and restriction are linear, so the correction equation has
+// the same composite operator), and adds e to u in float64.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -22,36 +30,47 @@ using namespace mgk;
 
 namespace {
 
+// Working buffers of one level in one precision.
+template <typename T>
+struct Bufs {
+  T* u[2] = {nullptr, nullptr};  // smoother double buffer; u[cur] is current
+  int cur = 0;
+  T* ffas = nullptr;             // working source
+  T* ubar = nullptr;             // restricted copy of this level's u (levels with a parent)
+  T* inter = nullptr;            // nests: tangential intermediate values
+  T* fc_unc = nullptr;           // nests: uncovered part of the parent face flux
+  // Periodic levels: every kernel that writes u also writes its ghost images,
+  // so ghosts are refilled only after u is loaded from outside.
+  bool ghosts_stale = true;
+};
+
 struct DevLevel {
   LevelGeom geo;
   Grid G;
   bool periodic = true;
   bool leaf = false;
-  bool has_child = false;
   Int3 off{0, 0, 0};  // origin in parent cells
   Int3 cn{0, 0, 0};   // covered extent in the parent
   Int3 child_lo{0, 0, 0}, child_hi{0, 0, 0};  // region covered by the child, own cells
-  double* u[2] = {nullptr, nullptr};
-  int cur = 0;
-  // Periodic levels: every kernel that writes u also writes its ghost images,
-  // so ghosts are refilled only after u is loaded from outside.
-  bool ghosts_stale = true;
-  double* f = nullptr;
-  double* ffas = nullptr;
-  double* ubar = nullptr;
+  Bufs<double> d;     // float64 state (MG_FP64: every level; MG_MIXED: leaf levels, u[0] only)
+  Bufs<float> s;      // float32 correction state (MG_MIXED only)
+  double* f = nullptr;     // leaf levels: float64 source
+  double* kern = nullptr;  // coarsest level: periodic pseudo-inverse kernel
   FaceSet fs;
-  double* inter = nullptr;
-  double* fc_unc = nullptr;
-  double* kern = nullptr;
   int nblocks = 0;
   int partial_off = 0;
 };
 
-struct Plan {
-  std::vector<LevelGeom> geo;
-  int base = 0;
-  size_t bytes = 0;
-};
+template <typename T>
+Bufs<T>& bufs(DevLevel& L);
+template <>
+Bufs<double>& bufs<double>(DevLevel& L) {
+  return L.d;
+}
+template <>
+Bufs<float>& bufs<float>(DevLevel& L) {
+  return L.s;
+}
 
 constexpr size_t kAlign = 256;
 
@@ -63,13 +82,48 @@ double centre_weight(int order) {
   return 3.0 * l[order / 2];
 }
 
+// Carves the arena; with base == nullptr it only counts bytes.
+struct Carver {
+  char* base = nullptr;
+  size_t used = 0;
+  template <typename T>
+  T* take(size_t count) {
+    T* p = base ? reinterpret_cast<T*>(base + used) : nullptr;
+    used += align_up(count * sizeof(T));
+    return p;
+  }
+};
+
+// A CUDA-event pair recorded around one timed launch inside a captured graph.
+struct ProfEv {
+  int fam;
+  cudaEvent_t a, b;
+};
+
+// One captured and instantiated cycle body with the launch counts it adds per
+// replay and the event pairs it records.
+struct Graph {
+  cudaGraphExec_t exec = nullptr;
+  unsigned mask = 0;
+  mg_stats delta;
+  std::vector<ProfEv> evs;
+};
+
 }  // namespace
 
 struct mg_hierarchy {
   mg_config cfg;
   std::vector<DevLevel> L;
   int base = 0;
-  cudaStream_t s = nullptr;
+  bool mixed = false;
+  cudaStream_t user_s = nullptr;  // the caller's stream
+  cudaStream_t s = nullptr;       // the hierarchy's own non-blocking work stream
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  // MG_FP64: V-cycle + norm; MG_MIXED: outer iteration + norm.  [0] launches
+  // plainly; [1] also records the profiling events (first cycle of each solve).
+  Graph g_cycle[2];
+  Graph* capturing = nullptr;     // graph being captured
+  Graph* replayed = nullptr;      // graph whose event pairs await reading
   CfWeights w;
   std::string err;
   void* arena = nullptr;
@@ -83,7 +137,8 @@ struct mg_hierarchy {
   double volume = 0.0;
   // launch counters and optional CUDA-event timing per kernel family
   mg_stats stats;
-  unsigned prof_mask = 0;
+  unsigned prof_mask = 0;    // families the caller asked to time
+  unsigned active_mask = 0;  // families timed by the launches being issued now
   std::vector<cudaEvent_t> ev_start[MG_K_FAMILIES], ev_end[MG_K_FAMILIES];
   size_t ev_used[MG_K_FAMILIES] = {0};
 };
@@ -114,7 +169,15 @@ mg_status fail_cuda(mg_hierarchy* h, cudaError_t e, const char* what) {
   } while (0)
 
 mg_status prof_begin(mg_hierarchy* h, int fam) {
-  if (!(h->prof_mask & (1u << fam))) return MG_OK;
+  if (!(h->active_mask & (1u << fam))) return MG_OK;
+  if (h->capturing) {
+    ProfEv ev{fam, nullptr, nullptr};
+    CK(cudaEventCreate(&ev.a));
+    CK(cudaEventCreate(&ev.b));
+    h->capturing->evs.push_back(ev);
+    CK(cudaEventRecordWithFlags(ev.a, h->s, cudaEventRecordExternal));
+    return MG_OK;
+  }
   size_t& used = h->ev_used[fam];
   if (used == h->ev_start[fam].size()) {
     cudaEvent_t a, b;
@@ -130,7 +193,11 @@ mg_status prof_begin(mg_hierarchy* h, int fam) {
 mg_status prof_end(mg_hierarchy* h, int fam, long long cells) {
   h->stats.launches[fam] += 1;
   h->stats.cells[fam] += cells;
-  if (!(h->prof_mask & (1u << fam))) return MG_OK;
+  if (!(h->active_mask & (1u << fam))) return MG_OK;
+  if (h->capturing) {
+    CK(cudaEventRecordWithFlags(h->capturing->evs.back().b, h->s, cudaEventRecordExternal));
+    return MG_OK;
+  }
   size_t& used = h->ev_used[fam];
   CK(cudaEventRecord(h->ev_end[fam][used], h->s));
   used += 1;
@@ -150,6 +217,101 @@ long long cells_of(const Grid& G) { return (long long)G.n0 * G.n1 * G.n2; }
 long long cells_of(Int3 c) { return (long long)c.x * c.y * c.z; }
 long long shell_of(const Grid& G) {
   return (long long)G.X * G.Y * (G.n2 + 2 * G.g) - cells_of(G);
+}
+
+struct Plan {
+  std::vector<LevelGeom> geo;
+  int base = 0;
+  size_t bytes = 0;
+};
+
+// Lays out every buffer of the hierarchy (counting only when h == nullptr).
+size_t carve(const mg_config* cfg, const Plan& p, mg_hierarchy* h, char* arena) {
+  Carver c;
+  c.base = arena;
+  const int g = cfg->order / 2;
+  const bool mixed = cfg->precision == MG_MIXED;
+  int slots = 0;
+  long long max_leaf = 0;
+  const size_t nl = p.geo.size();
+  for (size_t l = 0; l < nl; ++l) {
+    const LevelGeom& lg = p.geo[l];
+    const Grid G = make_grid(lg.n[0], lg.n[1], lg.n[2], g);
+    const size_t e = (size_t)grid_elems(G);
+    const bool leaf = (int)l >= p.base;
+    const size_t ncov = (size_t)(lg.n[0] / 2) * (lg.n[1] / 2) * (lg.n[2] / 2);
+    FaceSet fs;
+    make_faceset(G, g, &fs);
+    DevLevel* L = h ? &h->L[l] : nullptr;
+    if (!mixed) {
+      double* u0 = c.take<double>(e);
+      double* u1 = c.take<double>(e);
+      double* ff = c.take<double>(e);
+      double* ub = l > 0 ? c.take<double>(ncov) : nullptr;
+      double* in = lg.nest ? c.take<double>((size_t)fs.base[6]) : nullptr;
+      double* fu = lg.nest ? c.take<double>((size_t)fs.ebase[6]) : nullptr;
+      if (L) {
+        L->d.u[0] = u0;
+        L->d.u[1] = u1;
+        L->d.ffas = ff;
+        L->d.ubar = ub;
+        L->d.inter = in;
+        L->d.fc_unc = fu;
+      }
+    } else {
+      float* u0 = c.take<float>(e);
+      float* u1 = c.take<float>(e);
+      float* ff = c.take<float>(e);
+      float* ub = l > 0 ? c.take<float>(ncov) : nullptr;
+      float* in = lg.nest ? c.take<float>((size_t)fs.base[6]) : nullptr;
+      float* fu = lg.nest ? c.take<float>((size_t)fs.ebase[6]) : nullptr;
+      if (L) {
+        L->s.u[0] = u0;
+        L->s.u[1] = u1;
+        L->s.ffas = ff;
+        L->s.ubar = ub;
+        L->s.inter = in;
+        L->s.fc_unc = fu;
+      }
+      if (leaf) {
+        double* u0d = c.take<double>(e);
+        double* ind = lg.nest ? c.take<double>((size_t)fs.base[6]) : nullptr;
+        double* fud = lg.nest ? c.take<double>((size_t)fs.ebase[6]) : nullptr;
+        if (L) {
+          L->d.u[0] = u0d;
+          L->d.u[1] = nullptr;
+          L->d.inter = ind;
+          L->d.fc_unc = fud;
+        }
+      }
+    }
+    if (leaf) {
+      double* f = c.take<double>(e);
+      if (L) {
+        L->f = f;
+        L->nblocks = norm_blocks(G);
+        L->partial_off = slots;
+      }
+      slots += norm_blocks(G);
+      const long long dense = (long long)lg.n[0] * lg.n[1] * lg.n[2];
+      if (dense > max_leaf) max_leaf = dense;
+    }
+    if (l == 0) {
+      double* k = c.take<double>((size_t)lg.n[0] * lg.n[1] * lg.n[2]);
+      if (L) L->kern = k;
+    }
+  }
+  double* partial = c.take<double>((size_t)slots * 2);
+  double* red = c.take<double>(4);
+  double* scratch = c.take<double>((size_t)3 * max_leaf);
+  if (h) {
+    h->partial_slots = slots;
+    h->partial = partial;
+    h->red = red;
+    h->scratch = scratch;
+    h->scratch_elems = max_leaf;
+  }
+  return c.used;
 }
 
 bool validate(const mg_config* cfg, char* msg, size_t len, Plan* plan) {
@@ -178,8 +340,8 @@ bool validate(const mg_config* cfg, char* msg, size_t len, Plan* plan) {
     if (msg && len) snprintf(msg, len, "unknown precision %d", cfg->precision);
     return false;
   }
-  if (cfg->precision == MG_MIXED) {
-    if (msg && len) snprintf(msg, len, "MG_MIXED is not available in this build");
+  if (cfg->precision == MG_MIXED && (cfg->inner_cycles < 1 || cfg->inner_cycles > 16)) {
+    if (msg && len) snprintf(msg, len, "inner_cycles must be in [1, 16] for MG_MIXED");
     return false;
   }
   if (cfg->nu1 < 0 || cfg->nu2 < 0 || cfg->nu1 + cfg->nu2 < 1 || cfg->nu1 > 16 || cfg->nu2 > 16) {
@@ -200,178 +362,375 @@ bool validate(const mg_config* cfg, char* msg, size_t len, Plan* plan) {
   }
   Plan p;
   if (!build_levels(cfg, p.geo, &p.base, msg, len)) return false;
-  // bytes
-  const int g = cfg->order / 2;
-  size_t bytes = 0;
-  long long max_leaf = 0;
-  int slots = 0;
-  for (size_t l = 0; l < p.geo.size(); ++l) {
-    const LevelGeom& lg = p.geo[l];
-    const Grid G = make_grid(lg.n[0], lg.n[1], lg.n[2], g);
-    const size_t e = (size_t)grid_elems(G) * sizeof(double);
-    const bool leaf = (int)l >= p.base;
-    bytes += 3 * align_up(e);  // u[0], u[1], ffas
-    if (leaf) {
-      bytes += align_up(e);  // f
-      const long long dense = (long long)lg.n[0] * lg.n[1] * lg.n[2];
-      if (dense > max_leaf) max_leaf = dense;
-      slots += norm_blocks(G);
-    }
-    if (l > 0) bytes += align_up((size_t)(lg.n[0] / 2) * (lg.n[1] / 2) * (lg.n[2] / 2) * sizeof(double));
-    if (lg.nest) {
-      FaceSet fs;
-      make_faceset(G, g, &fs);
-      bytes += align_up((size_t)fs.base[6] * sizeof(double));
-      bytes += align_up((size_t)fs.ebase[6] * sizeof(double));
-    }
-    if (l == 0) bytes += align_up((size_t)lg.n[0] * lg.n[1] * lg.n[2] * sizeof(double));
-  }
-  bytes += align_up((size_t)slots * 2 * sizeof(double));
-  bytes += align_up(4 * sizeof(double));
-  bytes += align_up((size_t)3 * max_leaf * sizeof(double));
-  p.bytes = bytes;
+  p.bytes = carve(cfg, p, nullptr, nullptr);
   if (plan) *plan = p;
   return true;
 }
 
-// ---- level operations -------------------------------------------------------
+int finest(const mg_hierarchy* h) { return (int)h->L.size() - 1; }
+int n_leaf(const mg_hierarchy* h) { return (int)h->L.size() - h->base; }
 
+// ---- level operations, templated on the V-cycle precision --------------------
+
+template <typename T>
 mg_status tangential(mg_hierarchy* h, int l) {
   DevLevel& L = h->L[l];
   DevLevel& P = h->L[l - 1];
-  KL(MG_K_GHOST, L.fs.base[6], launch_cf_tangential<double>(h->cfg.order, L.G, P.G, P.u[P.cur], L.off, L.fs, h->w,
-                                  1.0 / P.geo.h, L.inter, L.fc_unc, h->s));
+  Bufs<T>& b = bufs<T>(L);
+  Bufs<T>& pb = bufs<T>(P);
+  KL(MG_K_GHOST, L.fs.base[6],
+     launch_cf_tangential<T>(h->cfg.order, L.G, P.G, pb.u[pb.cur], L.off, L.fs, h->w,
+                             1.0 / P.geo.h, b.inter, b.fc_unc, h->s));
   return MG_OK;
 }
 
+template <typename T>
 mg_status ghost_fill(mg_hierarchy* h, int l, bool edges) {
   DevLevel& L = h->L[l];
+  Bufs<T>& b = bufs<T>(L);
   if (L.periodic) {
-    if (L.ghosts_stale)
-      KL(MG_K_GHOST, shell_of(L.G), launch_ghost_periodic<double>(L.G, L.u[L.cur], h->s));
-    L.ghosts_stale = false;
+    if (b.ghosts_stale)
+      KL(MG_K_GHOST, shell_of(L.G), launch_ghost_periodic<T>(L.G, b.u[b.cur], h->s));
+    b.ghosts_stale = false;
     return MG_OK;
   }
   DevLevel& P = h->L[l - 1];
-  KL(MG_K_GHOST, 4 * L.fs.ebase[6] * L.G.g, launch_cf_flux<double>(h->cfg.order, L.G, L.u[L.cur], L.fs, h->w, L.inter, L.fc_unc,
-                            L.geo.h, 1.0 / L.geo.h, 1.0 / P.geo.h, 1, h->s));
+  Bufs<T>& pb = bufs<T>(P);
+  KL(MG_K_GHOST, 4 * L.fs.ebase[6] * L.G.g,
+     launch_cf_flux<T>(h->cfg.order, L.G, b.u[b.cur], L.fs, h->w, b.inter, b.fc_unc, L.geo.h,
+                       1.0 / L.geo.h, 1.0 / P.geo.h, 1, h->s));
   if (edges)
-    KL(MG_K_GHOST, shell_of(L.G), launch_cf_edges<double>(h->cfg.order, L.G, L.u[L.cur], P.G, P.u[P.cur], L.off, h->w, h->s));
+    KL(MG_K_GHOST, shell_of(L.G),
+       launch_cf_edges<T>(h->cfg.order, L.G, b.u[b.cur], P.G, pb.u[pb.cur], L.off, h->w, h->s));
   return MG_OK;
 }
 
+template <typename T>
 mg_status half_sweep(mg_hierarchy* h, int l, int colour) {
   DevLevel& L = h->L[l];
-  ST(ghost_fill(h, l, false));
+  Bufs<T>& b = bufs<T>(L);
+  ST(ghost_fill<T>(h, l, false));
   const double a_f = L.geo.h * L.geo.h / centre_weight(h->cfg.order);
-  KL(MG_K_SMOOTH, (cells_of(L.G) + 1) / 2, launch_smooth_half<double>(h->cfg.order, L.G, L.u[L.cur], L.u[1 - L.cur], L.ffas, a_f,
-                                colour, L.periodic ? 1 : 0, h->s));
-  L.cur ^= 1;
+  KL(MG_K_SMOOTH, (cells_of(L.G) + 1) / 2,
+     launch_smooth_half<T>(h->cfg.order, L.G, b.u[b.cur], b.u[1 - b.cur], b.ffas, a_f, colour,
+                           L.periodic ? 1 : 0, h->s));
+  b.cur ^= 1;
   return MG_OK;
 }
 
+template <typename T>
 mg_status smooth(mg_hierarchy* h, int l, int sweeps) {
   for (int s = 0; s < sweeps; ++s) {
-    ST(half_sweep(h, l, 0));
-    ST(half_sweep(h, l, 1));
+    ST(half_sweep<T>(h, l, 0));
+    ST(half_sweep<T>(h, l, 1));
   }
   return MG_OK;
 }
 
+template <typename T>
 mg_status vcycle(mg_hierarchy* h, int l) {
   DevLevel& L = h->L[l];
+  Bufs<T>& b = bufs<T>(L);
   const int order = h->cfg.order;
   if (l == 0) {
-    KL(MG_K_COARSEST, cells_of(L.G), launch_coarsest(L.G, L.ffas, L.u[L.cur], L.kern, h->s));
+    KL(MG_K_COARSEST, cells_of(L.G), launch_coarsest(L.G, b.ffas, b.u[b.cur], L.kern, h->s));
     return MG_OK;
   }
   DevLevel& P = h->L[l - 1];
-  ST(smooth(h, l, h->cfg.nu1));
-  ST(ghost_fill(h, l, false));
-  KL(MG_K_RESTRICT, cells_of(L.G), launch_residual_restrict<double>(order, L.G, L.u[L.cur], L.ffas, 1.0 / (L.geo.h * L.geo.h),
-                                      P.G, P.u[P.cur], P.ffas, L.ubar, L.off, L.cn,
-                                      P.periodic ? 1 : 0, h->s));
-  KL(MG_K_FAS, cells_of(L.cn), launch_fas_source<double>(order, P.G, P.u[P.cur], P.ffas, 1.0 / (P.geo.h * P.geo.h), L.off,
-                               L.cn, h->s));
-  ST(vcycle(h, l - 1));
-  if (!L.periodic) ST(tangential(h, l));
-  KL(MG_K_PROLONG, cells_of(L.G), launch_prolong<double>(L.G, L.u[L.cur], P.G, P.u[P.cur], L.ubar, L.off, L.cn,
-                                 L.periodic ? 1 : 0, h->s));
-  ST(smooth(h, l, h->cfg.nu2));
+  Bufs<T>& pb = bufs<T>(P);
+  ST(smooth<T>(h, l, h->cfg.nu1));
+  ST(ghost_fill<T>(h, l, false));
+  KL(MG_K_RESTRICT, cells_of(L.G),
+     launch_residual_restrict<T>(order, L.G, b.u[b.cur], b.ffas, 1.0 / (L.geo.h * L.geo.h), P.G,
+                                 pb.u[pb.cur], pb.ffas, b.ubar, L.off, L.cn,
+                                 P.periodic ? 1 : 0, h->s));
+  KL(MG_K_FAS, cells_of(L.cn),
+     launch_fas_source<T>(order, P.G, pb.u[pb.cur], pb.ffas, 1.0 / (P.geo.h * P.geo.h), L.off,
+                          L.cn, h->s));
+  ST(vcycle<T>(h, l - 1));
+  if (!L.periodic) ST(tangential<T>(h, l));
+  KL(MG_K_PROLONG, cells_of(L.G),
+     launch_prolong<T>(L.G, b.u[b.cur], P.G, pb.u[pb.cur], b.ubar, L.off, L.cn,
+                       L.periodic ? 1 : 0, h->s));
+  ST(smooth<T>(h, l, h->cfg.nu2));
   return MG_OK;
 }
 
-int finest(const mg_hierarchy* h) { return (int)h->L.size() - 1; }
+mg_status fill_zero(mg_hierarchy* h, double* p, long long e) {
+  KL(MG_K_COPY, e, launch_fill(p, e, 0.0, h->s));
+  return MG_OK;
+}
+
+mg_status fill_zero(mg_hierarchy* h, float* p, long long e) {
+  KL(MG_K_COPY, e, launch_fill_zero(p, e, h->s));
+  return MG_OK;
+}
+
+template <typename T>
+mg_status zero_state(mg_hierarchy* h, int from_level) {
+  for (int l = from_level; l <= finest(h); ++l) {
+    DevLevel& L = h->L[l];
+    Bufs<T>& b = bufs<T>(L);
+    const long long e = grid_elems(L.G);
+    for (int q = 0; q < 2; ++q)
+      if (b.u[q]) ST(fill_zero(h, b.u[q], e));
+    b.cur = 0;
+    b.ghosts_stale = false;
+  }
+  return MG_OK;
+}
+
+// ---- float64 leaf state: sync, norms, residual -------------------------------
+
+double* phi_of(DevLevel& L) { return L.d.u[L.d.cur]; }
 
 mg_status sync_covered(mg_hierarchy* h) {
   for (int l = finest(h); l > h->base; --l) {
     DevLevel& L = h->L[l];
     DevLevel& P = h->L[l - 1];
-    KL(MG_K_RESTRICT, cells_of(L.G), launch_restrict_u<double>(L.G, L.u[L.cur], P.G, P.u[P.cur], L.off, L.cn, h->s));
+    KL(MG_K_RESTRICT, cells_of(L.G),
+       launch_restrict_u<double>(L.G, phi_of(L), P.G, phi_of(P), L.off, L.cn, h->s));
   }
   return MG_OK;
 }
 
-// Leaf residual norm after syncing covered cells; reads 4 doubles back.
-mg_status leaf_norms(mg_hierarchy* h, double* rr, double* ff, double* fsum) {
+// Leaf residual norm after syncing covered cells, queued on the stream (no
+// host synchronisation, so it can be captured); ends with the copy of 4
+// doubles to pinned host memory.  In MG_MIXED the residual is also stored
+// (float32) as the correction source.
+mg_status norm_launches(mg_hierarchy* h) {
   ST(sync_covered(h));
   for (int l = h->base; l <= finest(h); ++l) {
     DevLevel& L = h->L[l];
-    ST(ghost_fill(h, l, false));
-    KL(MG_K_NORM, cells_of(L.G), launch_norm_partial(h->cfg.order, L.G, L.u[L.cur], L.f, 1.0 / (L.geo.h * L.geo.h),
+    ST(ghost_fill<double>(h, l, false));
+    KL(MG_K_NORM, cells_of(L.G),
+       launch_norm_partial(h->cfg.order, L.G, phi_of(L), L.f, 1.0 / (L.geo.h * L.geo.h),
                            L.geo.h * L.geo.h * L.geo.h, L.child_lo, L.child_hi,
-                           h->partial + 2 * L.partial_off, L.nblocks, h->s));
+                           h->partial + 2 * L.partial_off, L.nblocks,
+                           h->mixed ? L.s.ffas : nullptr, h->s));
   }
-  KL(MG_K_NORM, h->partial_slots, launch_reduce_partials(h->partial, h->partial_slots, 2, h->red, h->s));
+  KL(MG_K_NORM, h->partial_slots,
+     launch_reduce_partials(h->partial, h->partial_slots, 2, h->red, h->s));
   CK(cudaMemcpyAsync(h->host_red, h->red, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+  return MG_OK;
+}
+
+// Waits for the queued work, reads the norm record and the event pairs of the
+// graph just replayed.
+mg_status norm_read(mg_hierarchy* h, double* rr, double* ff, double* fsum) {
   CK(cudaStreamSynchronize(h->s));
+  if (h->replayed) {
+    for (const ProfEv& ev : h->replayed->evs) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, ev.a, ev.b));
+      h->stats.event_ms[ev.fam] += ms;
+      h->stats.timed[ev.fam] += 1;
+    }
+    h->replayed = nullptr;
+  }
   *rr = h->host_red[0];
   *ff = h->host_red[1];
   if (fsum) *fsum = h->host_red[2];
   return MG_OK;
 }
 
-// f on leaf levels holds the source; removes the composite mean, runs V-cycles.
-mg_status solve_prepared(mg_hierarchy* h, mg_info* info) {
+mg_status leaf_norms(mg_hierarchy* h, double* rr, double* ff, double* fsum) {
+  ST(norm_launches(h));
+  return norm_read(h, rr, ff, fsum);
+}
+
+void destroy_graph(Graph& g) {
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  g.exec = nullptr;
+  for (ProfEv& ev : g.evs) {
+    cudaEventDestroy(ev.a);
+    cudaEventDestroy(ev.b);
+  }
+  g.evs.clear();
+}
+
+// Runs body(h) once: directly, or by replaying the graph captured from it (the
+// body's launches depend only on the hierarchy, not on the cycle, because every
+// level returns to the same buffer parity after each visit).
+// With timed = true the profiled families carry CUDA events; the solve loops
+// time the first cycle of every solve, so every level's launches are sampled
+// once per solve without event overhead on the other cycles.
+template <typename Body>
+mg_status run_body(mg_hierarchy* h, bool timed, Body body) {
+  const unsigned mask = timed ? h->prof_mask : 0u;
+  Graph& g = h->g_cycle[timed && mask ? 1 : 0];
+  if (h->cfg.flags & MG_FLAG_NO_GRAPHS) {
+    const unsigned keep = h->active_mask;
+    h->active_mask = mask;
+    const mg_status st = body(h);
+    h->active_mask = keep;
+    return st;
+  }
+  if (!g.exec || g.mask != mask) {
+    destroy_graph(g);
+    const mg_stats snap = h->stats;
+    CK(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeRelaxed));
+    h->capturing = &g;
+    const unsigned keep = h->active_mask;
+    h->active_mask = mask;
+    const mg_status st = body(h);
+    h->active_mask = keep;
+    h->capturing = nullptr;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(h->s, &graph);
+    for (int f = 0; f < MG_K_FAMILIES; ++f) {
+      g.delta.launches[f] = h->stats.launches[f] - snap.launches[f];
+      g.delta.cells[f] = h->stats.cells[f] - snap.cells[f];
+      g.delta.event_ms[f] = 0.0;
+      g.delta.timed[f] = 0;
+    }
+    h->stats = snap;
+    if (st != MG_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      destroy_graph(g);
+      return st;
+    }
+    CK(e);
+    const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(ei);
+    g.mask = mask;
+  }
+  CK(cudaGraphLaunch(g.exec, h->s));
+  for (int f = 0; f < MG_K_FAMILIES; ++f) {
+    h->stats.launches[f] += g.delta.launches[f];
+    h->stats.cells[f] += g.delta.cells[f];
+  }
+  h->replayed = &g;
+  return MG_OK;
+}
+
+mg_status fp64_cycle_body(mg_hierarchy* h) {
+  ST(vcycle<double>(h, finest(h)));
+  return norm_launches(h);
+}
+
+mg_status mixed_outer_body(mg_hierarchy* h) {
+  ST(zero_state<float>(h, 0));
+  for (int l = h->base + 1; l <= finest(h); ++l) ST(tangential<float>(h, l));
+  for (int m = 0; m < h->cfg.inner_cycles; ++m) ST(vcycle<float>(h, finest(h)));
   for (int l = h->base; l <= finest(h); ++l) {
     DevLevel& L = h->L[l];
-    KL(MG_K_NORM, cells_of(L.G), launch_sum_partial(L.G, L.f, L.geo.h * L.geo.h * L.geo.h, L.child_lo, L.child_hi,
+    KL(MG_K_PROLONG, cells_of(L.G),
+       launch_add_correction(L.G, phi_of(L), L.s.u[L.s.cur], L.periodic ? 1 : 0, h->s));
+  }
+  for (int l = h->base + 1; l <= finest(h); ++l) ST(tangential<double>(h, l));
+  return norm_launches(h);
+}
+
+// f on the leaf levels holds the source: remove its composite mean.
+mg_status remove_source_mean(mg_hierarchy* h) {
+  for (int l = h->base; l <= finest(h); ++l) {
+    DevLevel& L = h->L[l];
+    KL(MG_K_NORM, cells_of(L.G),
+       launch_sum_partial(L.G, L.f, L.geo.h * L.geo.h * L.geo.h, L.child_lo, L.child_hi,
                           h->partial + 2 * L.partial_off, L.nblocks, h->s));
   }
-  KL(MG_K_NORM, h->partial_slots, launch_reduce_partials(h->partial, h->partial_slots, 2, h->red + 2, h->s));
+  KL(MG_K_NORM, h->partial_slots,
+     launch_reduce_partials(h->partial, h->partial_slots, 2, h->red + 2, h->s));
   for (int l = h->base; l <= finest(h); ++l) {
     DevLevel& L = h->L[l];
-    KL(MG_K_COPY, cells_of(L.G), launch_shift_copy(L.G, L.f, L.ffas, h->red + 2, 1.0 / h->volume, h->s));
+    KL(MG_K_COPY, cells_of(L.G),
+       launch_shift_copy(L.G, L.f, h->mixed ? nullptr : L.d.ffas, h->red + 2, 1.0 / h->volume,
+                         h->s));
   }
-  for (size_t l = 0; l < h->L.size(); ++l) {
-    DevLevel& L = h->L[l];
-    const long long e = grid_elems(L.G);
-    KL(MG_K_COPY, e, launch_fill(L.u[0], e, 0.0, h->s));
-    KL(MG_K_COPY, e, launch_fill(L.u[1], e, 0.0, h->s));
-    L.cur = 0;
-    L.ghosts_stale = false;
-  }
-  for (int l = h->base + 1; l <= finest(h); ++l) ST(tangential(h, l));
+  return MG_OK;
+}
+
+mg_status finish_info(mg_hierarchy* h, mg_info& local, double rel, mg_info* info) {
+  local.rel_residual = rel;
+  if (info) *info = local;
+  const bool fixed = !(h->cfg.tol > 0.0);
+  if (!std::isfinite(rel)) return fail(h, MG_ENOCONV, "residual is not finite");
+  if (!fixed && rel > h->cfg.tol) return fail(h, MG_ENOCONV, "max_cycles reached above tol");
+  return MG_OK;
+}
+
+void record(mg_info& local, double rel) {
+  if (local.cycles < MG_MAX_HISTORY) local.history[local.cycles] = rel;
+  local.cycles++;
+}
+
+mg_status solve_fp64(mg_hierarchy* h, mg_info* info) {
+  ST(remove_source_mean(h));
+  ST(zero_state<double>(h, 0));
+  for (int l = h->base + 1; l <= finest(h); ++l) ST(tangential<double>(h, l));
   mg_info local;
   std::memset(&local, 0, sizeof(local));
   double rel = INFINITY;
   const bool fixed = !(h->cfg.tol > 0.0);
   for (int c = 0; c < h->cfg.max_cycles; ++c) {
-    ST(vcycle(h, finest(h)));
+    ST(run_body(h, c == 0, fp64_cycle_body));
     double rr, ff, fs;
-    ST(leaf_norms(h, &rr, &ff, &fs));
+    ST(norm_read(h, &rr, &ff, &fs));
     if (c == 0) local.source_mean = fs / h->volume;
     rel = ff > 0.0 ? std::sqrt(rr) / std::sqrt(ff) : std::sqrt(rr);
-    if (local.cycles < MG_MAX_HISTORY) local.history[local.cycles] = rel;
-    local.cycles++;
+    record(local, rel);
     if (!std::isfinite(rel)) break;
     if (!fixed && rel <= h->cfg.tol) break;
   }
-  local.rel_residual = rel;
-  if (info) *info = local;
-  if (!std::isfinite(rel)) return fail(h, MG_ENOCONV, "residual is not finite");
-  if (!fixed && rel > h->cfg.tol) return fail(h, MG_ENOCONV, "max_cycles reached above tol");
+  return finish_info(h, local, rel, info);
+}
+
+mg_status solve_mixed(mg_hierarchy* h, mg_info* info) {
+  ST(remove_source_mean(h));
+  ST(zero_state<double>(h, h->base));
+  for (int l = h->base + 1; l <= finest(h); ++l) ST(tangential<double>(h, l));
+  mg_info local;
+  std::memset(&local, 0, sizeof(local));
+  double rr, ff, fs;
+  // the residual of u = 0 is the source; it becomes the first correction source
+  ST(leaf_norms(h, &rr, &ff, &fs));
+  local.source_mean = fs / h->volume;
+  double rel = ff > 0.0 ? std::sqrt(rr) / std::sqrt(ff) : std::sqrt(rr);
+  const bool fixed = !(h->cfg.tol > 0.0);
+  for (int c = 0; c < h->cfg.max_cycles; ++c) {
+    ST(run_body(h, c == 0, mixed_outer_body));
+    local.inner_cycles += h->cfg.inner_cycles;
+    ST(norm_read(h, &rr, &ff, &fs));
+    rel = ff > 0.0 ? std::sqrt(rr) / std::sqrt(ff) : std::sqrt(rr);
+    record(local, rel);
+    if (!std::isfinite(rel)) break;
+    if (!fixed && rel <= h->cfg.tol) break;
+  }
+  return finish_info(h, local, rel, info);
+}
+
+// The periodic problem fixes u only up to a constant.  The float64 V-cycle
+// converges to zero mean over the base level (covered cells holding the mean
+// of their children), the gauge its exact coarsest solve sets; the float64
+// residual of the mixed-precision refinement does not see constants, so its
+// result is shifted to the same gauge.
+mg_status gauge_zero_base_mean(mg_hierarchy* h) {
+  ST(sync_covered(h));
+  DevLevel& B = h->L[h->base];
+  const Int3 none{0, 0, 0};
+  KL(MG_K_NORM, cells_of(B.G),
+     launch_sum_partial(B.G, phi_of(B), 1.0, none, none, h->partial + 2 * B.partial_off,
+                        B.nblocks, h->s));
+  KL(MG_K_NORM, B.nblocks,
+     launch_reduce_partials(h->partial + 2 * B.partial_off, B.nblocks, 2, h->red + 2, h->s));
+  for (int l = h->base; l <= finest(h); ++l) {
+    DevLevel& L = h->L[l];
+    KL(MG_K_COPY, grid_elems(L.G),
+       launch_sub_mean(phi_of(L), grid_elems(L.G), h->red + 2, 1.0 / (double)cells_of(B.G),
+                       h->s));
+  }
+  for (int l = h->base + 1; l <= finest(h); ++l) ST(tangential<double>(h, l));
   return MG_OK;
+}
+
+mg_status solve_prepared(mg_hierarchy* h, mg_info* info) {
+  if (!h->mixed) return solve_fp64(h, info);
+  const mg_status st = solve_mixed(h, info);
+  if (st != MG_OK && st != MG_ENOCONV) return st;
+  ST(gauge_zero_base_mean(h));
+  return st;
 }
 
 cudaMemcpy3DParms dense_padded_parms(const DevLevel& L, double* padded, double* dense,
@@ -420,46 +779,49 @@ mg_status store_leaf(mg_hierarchy* h, int l, const double* padded, double* dst, 
   return MG_OK;
 }
 
-// phi (dense per leaf level) -> u[cur]; covered cells := mean of children.
+// phi (dense per leaf level) -> float64 u; covered cells := mean of children.
 mg_status load_potential(mg_hierarchy* h, const double* const phi[], bool host) {
   for (int l = h->base; l <= finest(h); ++l) {
     DevLevel& L = h->L[l];
-    ST(load_leaf(h, l, phi[l - h->base], L.u[L.cur], host));
-    L.ghosts_stale = true;
+    ST(load_leaf(h, l, phi[l - h->base], phi_of(L), host));
+    L.d.ghosts_stale = true;
   }
   ST(sync_covered(h));
-  for (int l = h->base + 1; l <= finest(h); ++l) ST(tangential(h, l));
+  for (int l = h->base + 1; l <= finest(h); ++l) ST(tangential<double>(h, l));
   return MG_OK;
 }
 
-// tau of the potential currently in u[cur] into f of every leaf level.
+// tau of the potential currently in the float64 u into f of every leaf level.
 mg_status tau_into_f(mg_hierarchy* h) {
   for (int l = h->base; l <= finest(h); ++l) {
     DevLevel& L = h->L[l];
-    ST(ghost_fill(h, l, true));
-    KL(MG_K_LPT, cells_of(L.G), launch_lpt2_source(h->cfg.order, L.G, L.u[L.cur], 1.0 / (L.geo.h * L.geo.h), L.f, h->s));
+    ST(ghost_fill<double>(h, l, true));
+    KL(MG_K_LPT, cells_of(L.G),
+       launch_lpt2_source(h->cfg.order, L.G, phi_of(L), 1.0 / (L.geo.h * L.geo.h), L.f, h->s));
   }
   for (int l = finest(h); l > h->base; --l) {
     DevLevel& L = h->L[l];
     DevLevel& P = h->L[l - 1];
-    KL(MG_K_RESTRICT, cells_of(L.G), launch_restrict_u<double>(L.G, L.f, P.G, P.f, L.off, L.cn, h->s));
+    KL(MG_K_RESTRICT, cells_of(L.G),
+       launch_restrict_u<double>(L.G, L.f, P.G, P.f, L.off, L.cn, h->s));
   }
   return MG_OK;
 }
 
-// -G phi of the potential in u[cur]; outputs dense, 3 per leaf level.
+// -G phi of the potential in the float64 u; outputs dense, 3 per leaf level.
 mg_status gradient_out(mg_hierarchy* h, double* const disp[], bool host) {
   for (int l = h->base; l <= finest(h); ++l) {
     DevLevel& L = h->L[l];
     const int i = l - h->base;
-    ST(ghost_fill(h, l, false));
+    ST(ghost_fill<double>(h, l, false));
     double* dx = disp[3 * i];
     double* dy = disp[3 * i + 1];
     double* dz = disp[3 * i + 2];
     const long long n = (long long)L.G.n0 * L.G.n1 * L.G.n2;
     if (host) {
       if (!dx && !dy && !dz) continue;
-      KL(MG_K_LPT, n, launch_gradient(h->cfg.order, L.G, L.u[L.cur], 1.0 / L.geo.h, h->scratch,
+      KL(MG_K_LPT, n,
+         launch_gradient(h->cfg.order, L.G, phi_of(L), 1.0 / L.geo.h, h->scratch,
                          h->scratch + n, h->scratch + 2 * n, h->s));
       for (int a = 0; a < 3; ++a)
         if (disp[3 * i + a])
@@ -467,21 +829,30 @@ mg_status gradient_out(mg_hierarchy* h, double* const disp[], bool host) {
                              cudaMemcpyDeviceToHost, h->s));
     } else {
       if (!dx || !dy || !dz) return fail(h, MG_EINVAL, "displacement output pointer is NULL");
-      KL(MG_K_LPT, n, launch_gradient(h->cfg.order, L.G, L.u[L.cur], 1.0 / L.geo.h, dx, dy, dz, h->s));
+      KL(MG_K_LPT, n, launch_gradient(h->cfg.order, L.G, phi_of(L), 1.0 / L.geo.h, dx, dy, dz, h->s));
     }
   }
   return MG_OK;
 }
 
-bool check_ptrs(mg_hierarchy* h, const void* const* p, int count) {
+// Orders the hierarchy's work stream after the caller's stream, runs f, then
+// orders the caller's stream after the work.
+template <typename F>
+mg_status on_streams(mg_hierarchy* h, F f) {
+  CK(cudaEventRecord(h->ev_in, h->user_s));
+  CK(cudaStreamWaitEvent(h->s, h->ev_in, 0));
+  const mg_status st = f();
+  CK(cudaEventRecord(h->ev_out, h->s));
+  CK(cudaStreamWaitEvent(h->user_s, h->ev_out, 0));
+  return st;
+}
+
+bool check_ptrs(const void* const* p, int count) {
   if (!p) return false;
   for (int i = 0; i < count; ++i)
     if (!p[i]) return false;
-  (void)h;
   return true;
 }
-
-int n_leaf(const mg_hierarchy* h) { return (int)h->L.size() - h->base; }
 
 }  // namespace
 
@@ -500,6 +871,7 @@ void mg_config_default(mg_config* cfg) {
   cfg->nu1 = 2;
   cfg->nu2 = 2;
   cfg->max_cycles = 50;
+  cfg->inner_cycles = 2;
   cfg->tol = 1e-10;
 }
 
@@ -520,11 +892,12 @@ int mg_total_levels(const mg_config* cfg) {
   return (int)p.geo.size();
 }
 
-const char* mg_version(void) { return "mgic-gb300 0.1 (sm_103a)"; }
+const char* mg_version(void) { return "mgic-gb300 0.2 (sm_103a)"; }
 
 mg_status mg_set_profiling(mg_hierarchy* h, unsigned mask) {
   if (!h) return MG_EINVAL;
   h->prof_mask = mask & ((1u << MG_K_FAMILIES) - 1u);
+  h->active_mask = h->prof_mask;
   return MG_OK;
 }
 
@@ -556,65 +929,46 @@ mg_status mg_hierarchy_create(const mg_config* cfg, void* cuda_stream, mg_hierar
   mg_hierarchy* h = new mg_hierarchy();
   std::memset(&h->stats, 0, sizeof(h->stats));
   h->cfg = *cfg;
-  h->s = (cudaStream_t)cuda_stream;
+  h->user_s = (cudaStream_t)cuda_stream;
   h->base = plan.base;
+  if (cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    mg_hierarchy_destroy(h);
+    return MG_ECUDA;
+  }
+  h->mixed = cfg->precision == MG_MIXED;
   const int order = cfg->order;
   const int g = order / 2;
   compute_cf_weights(order, &h->w);
-  // allocate
   if (cfg->dev_alloc) {
     h->arena = cfg->dev_alloc(plan.bytes, cfg->alloc_ctx);
     if (!h->arena) {
-      delete h;
+      mg_hierarchy_destroy(h);
       return MG_ENOMEM;
     }
   } else {
     cudaError_t e = cudaMalloc(&h->arena, plan.bytes);
     if (e != cudaSuccess) {
-      delete h;
+      h->arena = nullptr;
+      mg_hierarchy_destroy(h);
       return e == cudaErrorMemoryAllocation ? MG_ENOMEM : MG_ECUDA;
     }
   }
   h->arena_bytes = plan.bytes;
-  char* cursor = (char*)h->arena;
-  auto take = [&](size_t bytes) {
-    char* p = cursor;
-    cursor += align_up(bytes);
-    return (double*)p;
-  };
   const size_t nl = plan.geo.size();
   h->L.resize(nl);
-  int slots = 0;
-  long long max_leaf = 0;
   for (size_t l = 0; l < nl; ++l) {
     DevLevel& L = h->L[l];
     L.geo = plan.geo[l];
     L.G = make_grid(L.geo.n[0], L.geo.n[1], L.geo.n[2], g);
     L.periodic = !L.geo.nest;
     L.leaf = (int)l >= h->base;
-    L.has_child = l + 1 < nl;
     L.off = Int3{L.geo.off[0], L.geo.off[1], L.geo.off[2]};
     L.cn = Int3{L.geo.n[0] / 2, L.geo.n[1] / 2, L.geo.n[2] / 2};
-    const size_t e = (size_t)grid_elems(L.G) * sizeof(double);
-    L.u[0] = take(e);
-    L.u[1] = take(e);
-    L.ffas = take(e);
-    if (L.leaf) {
-      L.f = take(e);
-      const long long dense = (long long)L.geo.n[0] * L.geo.n[1] * L.geo.n[2];
-      if (dense > max_leaf) max_leaf = dense;
-      L.nblocks = norm_blocks(L.G);
-      L.partial_off = slots;
-      slots += L.nblocks;
-    }
-    if (l > 0) L.ubar = take((size_t)L.cn.x * L.cn.y * L.cn.z * sizeof(double));
-    if (L.geo.nest) {
-      make_faceset(L.G, g, &L.fs);
-      L.inter = take((size_t)L.fs.base[6] * sizeof(double));
-      L.fc_unc = take((size_t)L.fs.ebase[6] * sizeof(double));
-    }
-    if (l == 0) L.kern = take((size_t)L.geo.n[0] * L.geo.n[1] * L.geo.n[2] * sizeof(double));
+    make_faceset(L.G, g, &L.fs);
   }
+  carve(cfg, plan, h, (char*)h->arena);
   for (size_t l = 0; l + 1 < nl; ++l) {
     DevLevel& L = h->L[l];
     const DevLevel& C = h->L[l + 1];
@@ -623,11 +977,6 @@ mg_status mg_hierarchy_create(const mg_config* cfg, void* cuda_stream, mg_hierar
       L.child_hi = Int3{C.off.x + C.cn.x, C.off.y + C.cn.y, C.off.z + C.cn.z};
     }
   }
-  h->partial_slots = slots;
-  h->partial = take((size_t)slots * 2 * sizeof(double));
-  h->red = take(4 * sizeof(double));
-  h->scratch_elems = max_leaf;
-  h->scratch = take((size_t)3 * max_leaf * sizeof(double));
   const LevelGeom& b = plan.geo[plan.base];
   h->volume = b.h * b.h * b.h * (double)b.n[0] * b.n[1] * b.n[2];
   cudaError_t e = cudaMallocHost(&h->host_red, 4 * sizeof(double));
@@ -652,7 +1001,8 @@ mg_status mg_hierarchy_create(const mg_config* cfg, void* cuda_stream, mg_hierar
 mg_status mg_hierarchy_destroy(mg_hierarchy* h) {
   if (!h) return MG_OK;
   if (h->s) cudaStreamSynchronize(h->s);
-  else cudaDeviceSynchronize();
+  destroy_graph(h->g_cycle[0]);
+  destroy_graph(h->g_cycle[1]);
   if (h->arena) {
     if (h->cfg.dev_free) h->cfg.dev_free(h->arena, h->cfg.alloc_ctx);
     else cudaFree(h->arena);
@@ -662,6 +1012,9 @@ mg_status mg_hierarchy_destroy(mg_hierarchy* h) {
     for (cudaEvent_t e : h->ev_start[f]) cudaEventDestroy(e);
     for (cudaEvent_t e : h->ev_end[f]) cudaEventDestroy(e);
   }
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_out) cudaEventDestroy(h->ev_out);
+  if (h->s) cudaStreamDestroy(h->s);
   delete h;
   return MG_OK;
 }
@@ -670,54 +1023,62 @@ mg_status mg_solve_1lpt(mg_hierarchy* h, const double* const delta[], double* co
                         mg_info* info) {
   if (!h) return MG_EINVAL;
   const int nleaf = n_leaf(h);
-  if (!check_ptrs(h, (const void* const*)delta, nleaf) || !check_ptrs(h, (const void* const*)phi, nleaf))
+  if (!check_ptrs((const void* const*)delta, nleaf) || !check_ptrs((const void* const*)phi, nleaf))
     return fail(h, MG_EINVAL, "delta/phi must hold one non-NULL pointer per level");
-  for (int l = h->base; l <= finest(h); ++l) ST(load_leaf(h, l, delta[l - h->base], h->L[l].f, false));
-  const mg_status st = solve_prepared(h, info);
-  if (st != MG_OK && st != MG_ENOCONV) return st;
-  for (int l = h->base; l <= finest(h); ++l)
-    ST(store_leaf(h, l, h->L[l].u[h->L[l].cur], phi[l - h->base], false));
-  CK(cudaStreamSynchronize(h->s));
-  return st;
+  return on_streams(h, [&]() -> mg_status {
+    for (int l = h->base; l <= finest(h); ++l) ST(load_leaf(h, l, delta[l - h->base], h->L[l].f, false));
+    const mg_status st = solve_prepared(h, info);
+    if (st != MG_OK && st != MG_ENOCONV) return st;
+    for (int l = h->base; l <= finest(h); ++l)
+      ST(store_leaf(h, l, phi_of(h->L[l]), phi[l - h->base], false));
+    CK(cudaStreamSynchronize(h->s));
+    return st;
+  });
 }
 
 mg_status mg_lpt2_source(mg_hierarchy* h, const double* const phi1[], double* const tau[]) {
   if (!h) return MG_EINVAL;
   const int nleaf = n_leaf(h);
-  if (!check_ptrs(h, (const void* const*)phi1, nleaf) || !check_ptrs(h, (const void* const*)tau, nleaf))
+  if (!check_ptrs((const void* const*)phi1, nleaf) || !check_ptrs((const void* const*)tau, nleaf))
     return fail(h, MG_EINVAL, "phi1/tau must hold one non-NULL pointer per level");
-  ST(load_potential(h, phi1, false));
-  ST(tau_into_f(h));
-  for (int l = h->base; l <= finest(h); ++l) ST(store_leaf(h, l, h->L[l].f, tau[l - h->base], false));
-  CK(cudaStreamSynchronize(h->s));
-  return MG_OK;
+  return on_streams(h, [&]() -> mg_status {
+    ST(load_potential(h, phi1, false));
+    ST(tau_into_f(h));
+    for (int l = h->base; l <= finest(h); ++l) ST(store_leaf(h, l, h->L[l].f, tau[l - h->base], false));
+    CK(cudaStreamSynchronize(h->s));
+    return MG_OK;
+  });
 }
 
 mg_status mg_solve_2lpt(mg_hierarchy* h, const double* const phi1[], double* const phi2[],
                         mg_info* info) {
   if (!h) return MG_EINVAL;
   const int nleaf = n_leaf(h);
-  if (!check_ptrs(h, (const void* const*)phi1, nleaf) || !check_ptrs(h, (const void* const*)phi2, nleaf))
+  if (!check_ptrs((const void* const*)phi1, nleaf) || !check_ptrs((const void* const*)phi2, nleaf))
     return fail(h, MG_EINVAL, "phi1/phi2 must hold one non-NULL pointer per level");
-  ST(load_potential(h, phi1, false));
-  ST(tau_into_f(h));
-  const mg_status st = solve_prepared(h, info);
-  if (st != MG_OK && st != MG_ENOCONV) return st;
-  for (int l = h->base; l <= finest(h); ++l)
-    ST(store_leaf(h, l, h->L[l].u[h->L[l].cur], phi2[l - h->base], false));
-  CK(cudaStreamSynchronize(h->s));
-  return st;
+  return on_streams(h, [&]() -> mg_status {
+    ST(load_potential(h, phi1, false));
+    ST(tau_into_f(h));
+    const mg_status st = solve_prepared(h, info);
+    if (st != MG_OK && st != MG_ENOCONV) return st;
+    for (int l = h->base; l <= finest(h); ++l)
+      ST(store_leaf(h, l, phi_of(h->L[l]), phi2[l - h->base], false));
+    CK(cudaStreamSynchronize(h->s));
+    return st;
+  });
 }
 
 mg_status mg_displacements(mg_hierarchy* h, const double* const phi[], double* const disp[]) {
   if (!h) return MG_EINVAL;
   const int nleaf = n_leaf(h);
-  if (!check_ptrs(h, (const void* const*)phi, nleaf) || !check_ptrs(h, (const void* const*)disp, 3 * nleaf))
+  if (!check_ptrs((const void* const*)phi, nleaf) || !check_ptrs((const void* const*)disp, 3 * nleaf))
     return fail(h, MG_EINVAL, "phi/disp must hold 1 and 3 non-NULL pointers per level");
-  ST(load_potential(h, phi, false));
-  ST(gradient_out(h, disp, false));
-  CK(cudaStreamSynchronize(h->s));
-  return MG_OK;
+  return on_streams(h, [&]() -> mg_status {
+    ST(load_potential(h, phi, false));
+    ST(gradient_out(h, disp, false));
+    CK(cudaStreamSynchronize(h->s));
+    return MG_OK;
+  });
 }
 
 mg_status mg_lpt_pipeline(mg_hierarchy* h, int host_buffers, const double* const delta[],
@@ -726,29 +1087,31 @@ mg_status mg_lpt_pipeline(mg_hierarchy* h, int host_buffers, const double* const
   if (!h) return MG_EINVAL;
   const bool host = host_buffers != 0;
   const int nleaf = n_leaf(h);
-  if (!check_ptrs(h, (const void* const*)delta, nleaf))
+  if (!check_ptrs((const void* const*)delta, nleaf))
     return fail(h, MG_EINVAL, "delta must hold one non-NULL pointer per level");
   if (!host) {
-    if (!check_ptrs(h, (const void* const*)disp1, 3 * nleaf) ||
-        !check_ptrs(h, (const void* const*)disp2, 3 * nleaf))
+    if (!check_ptrs((const void* const*)disp1, 3 * nleaf) ||
+        !check_ptrs((const void* const*)disp2, 3 * nleaf))
       return fail(h, MG_EINVAL, "device displacement outputs must all be set");
   }
-  for (int l = h->base; l <= finest(h); ++l) ST(load_leaf(h, l, delta[l - h->base], h->L[l].f, host));
-  mg_status st1 = solve_prepared(h, info1);
-  if (st1 != MG_OK && st1 != MG_ENOCONV) return st1;
-  if (phi1)
-    for (int l = h->base; l <= finest(h); ++l)
-      if (phi1[l - h->base]) ST(store_leaf(h, l, h->L[l].u[h->L[l].cur], phi1[l - h->base], host));
-  if (disp1) ST(gradient_out(h, disp1, host));
-  ST(tau_into_f(h));
-  mg_status st2 = solve_prepared(h, info2);
-  if (st2 != MG_OK && st2 != MG_ENOCONV) return st2;
-  if (phi2)
-    for (int l = h->base; l <= finest(h); ++l)
-      if (phi2[l - h->base]) ST(store_leaf(h, l, h->L[l].u[h->L[l].cur], phi2[l - h->base], host));
-  if (disp2) ST(gradient_out(h, disp2, host));
-  CK(cudaStreamSynchronize(h->s));
-  return st1 != MG_OK ? st1 : st2;
+  return on_streams(h, [&]() -> mg_status {
+    for (int l = h->base; l <= finest(h); ++l) ST(load_leaf(h, l, delta[l - h->base], h->L[l].f, host));
+    mg_status st1 = solve_prepared(h, info1);
+    if (st1 != MG_OK && st1 != MG_ENOCONV) return st1;
+    if (phi1)
+      for (int l = h->base; l <= finest(h); ++l)
+        if (phi1[l - h->base]) ST(store_leaf(h, l, phi_of(h->L[l]), phi1[l - h->base], host));
+    if (disp1) ST(gradient_out(h, disp1, host));
+    ST(tau_into_f(h));
+    mg_status st2 = solve_prepared(h, info2);
+    if (st2 != MG_OK && st2 != MG_ENOCONV) return st2;
+    if (phi2)
+      for (int l = h->base; l <= finest(h); ++l)
+        if (phi2[l - h->base]) ST(store_leaf(h, l, phi_of(h->L[l]), phi2[l - h->base], host));
+    if (disp2) ST(gradient_out(h, disp2, host));
+    CK(cudaStreamSynchronize(h->s));
+    return st1 != MG_OK ? st1 : st2;
+  });
 }
 
 }  // extern "C"

@@ -91,11 +91,23 @@ cudaError_t launch_cf_edges(int order, const Grid& F, T* u, const Grid& P, const
 // ---- kernels: coarsest solve, norms, packing, 2LPT, gradient (mg_misc.cu) ----
 cudaError_t launch_coarsest(const Grid& G, const double* f, double* u, const double* kern,
                             cudaStream_t s);
+// float32 source and result, float64 arithmetic (mixed precision keeps the coarsest
+// solve in float64)
+cudaError_t launch_coarsest(const Grid& G, const float* f, float* u, const double* kern,
+                            cudaStream_t s);
 // partial sums over uncovered interior cells of level G: [2*b] = sum r^2, [2*b+1] = sum f^2
 // (times vol), r = f - L u; blocks = number of partial slots written.
+// With r32 != nullptr the residual of every interior cell is also written to r32
+// (float32, same layout) as the source of the mixed-precision correction equation.
 cudaError_t launch_norm_partial(int order, const Grid& G, const double* u, const double* f,
                                 double invh2, double vol, Int3 clo, Int3 chi, double* partial,
-                                int blocks, cudaStream_t s);
+                                int blocks, float* r32, cudaStream_t s);
+cudaError_t launch_add_correction(const Grid& G, double* u, const float* e, int periodic,
+                                  cudaStream_t s);
+cudaError_t launch_fill_zero(float* p, long long n, cudaStream_t s);
+// p[0..n) -= sum[0] * scale, with sum on the device
+cudaError_t launch_sub_mean(double* p, long long n, const double* sum, double scale,
+                            cudaStream_t s);
 cudaError_t launch_sum_partial(const Grid& G, const double* f, double vol, Int3 clo, Int3 chi,
                                double* partial, int blocks, cudaStream_t s);
 cudaError_t launch_reduce_partials(const double* partial, int count, int width, double* out,

@@ -43,8 +43,9 @@ __device__ __forceinline__ double lap_w(int s) {
 // result is also written to the cell's periodic ghost images.
 constexpr int kCoarseBlock = 128;
 
+template <typename T>
 __global__ void __launch_bounds__(kCoarseBlock)
-    k_coarsest(Grid G, const double* __restrict__ f, double* __restrict__ u,
+    k_coarsest(Grid G, const T* __restrict__ f, T* __restrict__ u,
                const double* __restrict__ kern) {
   const int n12 = G.n1 * G.n2;
   const int n = G.n0 * n12;
@@ -57,7 +58,7 @@ __global__ void __launch_bounds__(kCoarseBlock)
     di += di < 0 ? G.n0 : 0;
     dj += dj < 0 ? G.n1 : 0;
     dk += dk < 0 ? G.n2 : 0;
-    acc = fma(__ldg(kern + (di * G.n1 + dj) * G.n2 + dk), __ldg(f + gidx(G, yi, yj, yk)), acc);
+    acc = fma(__ldg(kern + (di * G.n1 + dj) * G.n2 + dk), (double)__ldg(f + gidx(G, yi, yj, yk)), acc);
   }
   __shared__ double red[kCoarseBlock];
   red[threadIdx.x] = acc;
@@ -68,8 +69,9 @@ __global__ void __launch_bounds__(kCoarseBlock)
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    u[gidx(G, xi, xj, xk)] = red[0];
-    write_images<double>(G, u, xi, xj, xk, red[0]);
+    const T v = (T)red[0];
+    u[gidx(G, xi, xj, xk)] = v;
+    write_images<T>(G, u, xi, xj, xk, v);
   }
 }
 
@@ -95,10 +97,14 @@ constexpr int kRedBlock = 256;
 
 // One block per (x plane, 8 y rows); 32 lanes stride along z.  Block b writes
 // its partial sums to slot b, so the reduction order is fixed.
+// With r32 != nullptr the float64 residual of every interior cell is also
+// stored, rounded to float32, as the source of the correction equation
+// (mixed precision); the sums still skip covered cells.
 template <int ORDER>
 __global__ void __launch_bounds__(kRedBlock)
     k_norm_partial(Grid G, const double* __restrict__ u, const double* __restrict__ f,
-                   double invh2, double vol, Int3 clo, Int3 chi, double* __restrict__ partial) {
+                   double invh2, double vol, Int3 clo, Int3 chi, double* __restrict__ partial,
+                   float* __restrict__ r32) {
   const long long sy = G.Zp, sx = (long long)G.Y * G.Zp;
   const int i = blockIdx.y;
   const int j = blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -108,10 +114,13 @@ __global__ void __launch_bounds__(kRedBlock)
     const bool row_cov = i >= clo.x && i < chi.x && j >= clo.y && j < chi.y;
     const long long row = gidx(G, i, j, 0);
     for (int k = lane; k < G.n2; k += 32) {
-      if (row_cov && k >= clo.z && k < chi.z) continue;
+      const bool cov = row_cov && k >= clo.z && k < chi.z;
+      if (cov && !r32) continue;
       const long long p = row + k;
       const double fv = __ldg(f + p);
       const double r = fma(-invh2, lap_h2<ORDER, double>(u, p, sy, sx), fv);
+      if (r32) r32[p] = (float)r;
+      if (cov) continue;
       rr = fma(r, r, rr);
       ff = fma(fv, fv, ff);
     }
@@ -191,7 +200,33 @@ __global__ void __launch_bounds__(256)
   const long long p = gidx(G, i, j, k);
   const double v = f[p] - mean_num[0] * inv_volume;
   f[p] = v;
-  f2[p] = v;
+  if (f2) f2[p] = v;
+}
+
+// u += e on the interior (float64 += float32 correction); periodic levels also
+// update their ghost images.  One thread per cell of a (32 x 4)-cell tile row.
+__global__ void __launch_bounds__(128)
+    k_add_correction(Grid G, double* __restrict__ u, const float* __restrict__ e, int periodic) {
+  const int k = blockIdx.x * 32 + threadIdx.x;
+  const int j = blockIdx.y * 4 + threadIdx.y;
+  const int i = blockIdx.z;
+  if (k >= G.n2 || j >= G.n1) return;
+  const long long p = gidx(G, i, j, k);
+  const double v = u[p] + (double)__ldg(e + p);
+  u[p] = v;
+  if (periodic) write_images<double>(G, u, i, j, k, v);
+}
+
+// p -= sum[0] * scale over n elements (sum read on the device).
+__global__ void __launch_bounds__(256)
+    k_sub_mean(double* __restrict__ p, long long n, const double* __restrict__ sum, double scale) {
+  const long long t = blockIdx.x * 256LL + threadIdx.x;
+  if (t < n) p[t] -= sum[0] * scale;
+}
+
+__global__ void __launch_bounds__(256) k_fill_f32(float* __restrict__ p, long long n) {
+  const long long t = blockIdx.x * 256LL + threadIdx.x;
+  if (t < n) p[t] = 0.0f;
 }
 
 __global__ void __launch_bounds__(256) k_fill(double* __restrict__ p, long long n, double v) {
@@ -274,19 +309,26 @@ int norm_blocks(const Grid& G) { return ((G.n1 + 7) / 8) * G.n0; }
 cudaError_t launch_coarsest(const Grid& G, const double* f, double* u, const double* kern,
                             cudaStream_t s) {
   const int n = G.n0 * G.n1 * G.n2;
-  k_coarsest<<<n, kCoarseBlock, 0, s>>>(G, f, u, kern);
+  k_coarsest<double><<<n, kCoarseBlock, 0, s>>>(G, f, u, kern);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarsest(const Grid& G, const float* f, float* u, const double* kern,
+                            cudaStream_t s) {
+  const int n = G.n0 * G.n1 * G.n2;
+  k_coarsest<float><<<n, kCoarseBlock, 0, s>>>(G, f, u, kern);
   return cudaGetLastError();
 }
 
 cudaError_t launch_norm_partial(int order, const Grid& G, const double* u, const double* f,
                                 double invh2, double vol, Int3 clo, Int3 chi, double* partial,
-                                int blocks, cudaStream_t s) {
+                                int blocks, float* r32, cudaStream_t s) {
   const dim3 grid((G.n1 + 7) / 8, G.n0);
   if ((int)(grid.x * grid.y) != blocks) return cudaErrorInvalidValue;
   switch (order) {
-    case 2: k_norm_partial<2><<<grid, kRedBlock, 0, s>>>(G, u, f, invh2, vol, clo, chi, partial); break;
-    case 4: k_norm_partial<4><<<grid, kRedBlock, 0, s>>>(G, u, f, invh2, vol, clo, chi, partial); break;
-    case 6: k_norm_partial<6><<<grid, kRedBlock, 0, s>>>(G, u, f, invh2, vol, clo, chi, partial); break;
+    case 2: k_norm_partial<2><<<grid, kRedBlock, 0, s>>>(G, u, f, invh2, vol, clo, chi, partial, r32); break;
+    case 4: k_norm_partial<4><<<grid, kRedBlock, 0, s>>>(G, u, f, invh2, vol, clo, chi, partial, r32); break;
+    case 6: k_norm_partial<6><<<grid, kRedBlock, 0, s>>>(G, u, f, invh2, vol, clo, chi, partial, r32); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -324,6 +366,27 @@ cudaError_t launch_shift_copy(const Grid& G, double* f, double* f2, const double
                               double inv_volume, cudaStream_t s) {
   const long long n = (long long)G.n0 * G.n1 * G.n2;
   k_shift_copy<<<blocks_for(n, 256), 256, 0, s>>>(G, f, f2, mean_num, inv_volume);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_correction(const Grid& G, double* u, const float* e, int periodic,
+                                  cudaStream_t s) {
+  dim3 block(32, 4, 1);
+  dim3 grid((G.n2 + 31) / 32, (G.n1 + 3) / 4, G.n0);
+  k_add_correction<<<grid, block, 0, s>>>(G, u, e, periodic);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sub_mean(double* p, long long n, const double* sum, double scale,
+                            cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_sub_mean<<<blocks_for(n, 256), 256, 0, s>>>(p, n, sum, scale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_zero(float* p, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_fill_f32<<<blocks_for(n, 256), 256, 0, s>>>(p, n);
   return cudaGetLastError();
 }
 

@@ -13,6 +13,7 @@ MG_MAX_LEVELS = 16
 MG_MAX_HISTORY = 64
 MG_FP64 = 0
 MG_MIXED = 1
+MG_FLAG_NO_GRAPHS = 1
 
 STATUS = {0: "MG_OK", 1: "MG_EINVAL", 2: "MG_ENOMEM", 3: "MG_ENOCONV", 4: "MG_ECUDA",
           5: "MG_ETIMEOUT"}
@@ -33,6 +34,8 @@ class MGConfig(ctypes.Structure):
         ("nu1", ctypes.c_int),
         ("nu2", ctypes.c_int),
         ("max_cycles", ctypes.c_int),
+        ("inner_cycles", ctypes.c_int),
+        ("flags", ctypes.c_int),
         ("tol", ctypes.c_double),
         ("dev_alloc", _ALLOC_FN),
         ("dev_free", _FREE_FN),
@@ -46,11 +49,12 @@ class MGInfo(ctypes.Structure):
         ("rel_residual", ctypes.c_double),
         ("source_mean", ctypes.c_double),
         ("history", ctypes.c_double * MG_MAX_HISTORY),
+        ("inner_cycles", ctypes.c_int),
     ]
 
     def as_dict(self):
         return {"cycles": self.cycles, "rel_residual": self.rel_residual,
-                "source_mean": self.source_mean,
+                "source_mean": self.source_mean, "inner_cycles": self.inner_cycles,
                 "history": [self.history[i] for i in range(min(self.cycles, MG_MAX_HISTORY))]}
 
 
@@ -121,7 +125,7 @@ def load_library(path=None):
 
 
 def make_config(base_n, box, order, nests=(), precision=MG_FP64, nu1=2, nu2=2, max_cycles=50,
-                tol=1e-10):
+                tol=1e-10, inner_cycles=2, graphs=True):
     """MGConfig from plain values; nests = [(n3, off3), ...] (off in parent cells)."""
     lib = load_library()
     cfg = MGConfig()
@@ -137,6 +141,8 @@ def make_config(base_n, box, order, nests=(), precision=MG_FP64, nu1=2, nu2=2, m
     cfg.order = int(order)
     cfg.precision = int(precision)
     cfg.nu1, cfg.nu2, cfg.max_cycles, cfg.tol = int(nu1), int(nu2), int(max_cycles), float(tol)
+    cfg.inner_cycles = int(inner_cycles)
+    cfg.flags = 0 if graphs else MG_FLAG_NO_GRAPHS
     return cfg
 
 

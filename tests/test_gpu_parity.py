@@ -205,3 +205,39 @@ def test_bench_tolerance_gives_1e6_error(lib):
         for x, y in zip(a[key], b[key]):
             assert rel(x, y.cpu().numpy()) <= 1e-6, key
     assert i1["cycles"] + i2["cycles"] == bench.CYCLES_PER_STEP
+
+
+@pytest.mark.parametrize("order", (2, 4, 6))
+def test_mixed_precision_matches_fp64_oracle(lib, order):
+    """MG_MIXED (float32 V-cycles inside float64 iterative refinement) reaches the
+    float64 oracle's converged solution to <= 1e-6 RMS relative error in phi1, phi2
+    and both displacement fields."""
+    geom = small_zoom(24, ((20, 7), (16, 6)), order=order, box=50.0)
+    deltas = make_delta(geom, 31)
+    ref = lpt_pipeline(geom, deltas, tol=1e-12, max_cycles=40)
+    h = hier(lib, geom, tol=1e-10, precision=lib.MG_MIXED, inner_cycles=2)
+    out, i1, i2 = h.pipeline(to_dev(deltas))
+    assert i1["rel_residual"] <= 1e-10 and i2["rel_residual"] <= 1e-10
+    assert i1["inner_cycles"] == 2 * i1["cycles"]
+    for l in range(geom.n_levels):
+        assert rel(out["phi1"][l], ref["phi1"][l]) <= 1e-6
+        assert rel(out["phi2"][l], ref["phi2"][l]) <= 1e-6
+        for a in range(3):
+            assert rel(out["disp1"][3 * l + a], ref["psi1"][l][a]) <= 1e-6
+            assert rel(out["disp2"][3 * l + a], ref["psi2"][l][a]) <= 1e-6
+
+
+def test_mixed_precision_bench_workload(lib):
+    """On the benchmark workload at its stopping tolerance the mixed-precision step
+    stays within 1e-6 RMS relative error of tightly converged float64 solves."""
+    import bench
+    geom = config_zoom2()
+    deltas = to_dev(make_delta(geom, bench.SEED))
+    mixed = hier(lib, geom, tol=bench.SOLVE_TOL, precision=lib.MG_MIXED,
+                 inner_cycles=bench.MIXED_INNER_CYCLES)
+    tight = hier(lib, geom, tol=1e-12)
+    a, i1, i2 = mixed.pipeline(deltas)
+    b, _, _ = tight.pipeline(deltas)
+    for key in ("phi1", "phi2", "disp1", "disp2"):
+        for x, y in zip(a[key], b[key]):
+            assert rel(x, y.cpu().numpy()) <= 1e-6, key

@@ -156,7 +156,7 @@ mg_status mg_lpt_pipeline(mg_hierarchy* h, int host_buffers, const double* const
  *   phi, tau  caller-owned device arrays, dense float64 [n0][n1][n2]
  *   box       length of axis 0 (h = box / n0); order 2, 4 or 6
  *   err       optional message buffer of len bytes
- * Working memory is one static device array of 6 MiB (two ghost-padded grids,
+ * Working memory is one static device array of 16 MiB (five ghost-padded grids,
  * about 64^3 cells at order 6); larger grids return MG_EINVAL with a message.
  * The first call on each device looks up the array's address and should be
  * made outside stream capture.  Calls share the array: calls whose work

@@ -134,6 +134,7 @@ struct mg_hierarchy {
   double* host_red = nullptr;  // pinned copy of red
   double* scratch = nullptr;   // 3 dense arrays of the largest leaf level
   long long scratch_elems = 0;
+  double* tau_work = nullptr;  // 3 padded float64 arrays of the largest leaf level
   double volume = 0.0;
   // launch counters and optional CUDA-event timing per kernel family
   mg_stats stats;
@@ -233,6 +234,7 @@ size_t carve(const mg_config* cfg, const Plan& p, mg_hierarchy* h, char* arena) 
   const bool mixed = cfg->precision == MG_MIXED;
   int slots = 0;
   long long max_leaf = 0;
+  long long max_leaf_padded = 0;
   const size_t nl = p.geo.size();
   for (size_t l = 0; l < nl; ++l) {
     const LevelGeom& lg = p.geo[l];
@@ -295,6 +297,7 @@ size_t carve(const mg_config* cfg, const Plan& p, mg_hierarchy* h, char* arena) 
       slots += norm_blocks(G);
       const long long dense = (long long)lg.n[0] * lg.n[1] * lg.n[2];
       if (dense > max_leaf) max_leaf = dense;
+      if ((long long)e > max_leaf_padded) max_leaf_padded = (long long)e;
     }
     if (l == 0) {
       double* k = c.take<double>((size_t)lg.n[0] * lg.n[1] * lg.n[2]);
@@ -304,7 +307,9 @@ size_t carve(const mg_config* cfg, const Plan& p, mg_hierarchy* h, char* arena) 
   double* partial = c.take<double>((size_t)slots * 2);
   double* red = c.take<double>(4);
   double* scratch = c.take<double>((size_t)3 * max_leaf);
+  double* tau_work = c.take<double>((size_t)3 * max_leaf_padded);
   if (h) {
+    h->tau_work = tau_work;
     h->partial_slots = slots;
     h->partial = partial;
     h->red = red;
@@ -797,7 +802,8 @@ mg_status tau_into_f(mg_hierarchy* h) {
     DevLevel& L = h->L[l];
     ST(ghost_fill<double>(h, l, true));
     KL(MG_K_LPT, cells_of(L.G),
-       launch_lpt2_source(h->cfg.order, L.G, phi_of(L), 1.0 / (L.geo.h * L.geo.h), L.f, h->s));
+       launch_lpt2_source(h->cfg.order, L.G, phi_of(L), 1.0 / (L.geo.h * L.geo.h), L.f,
+                          h->tau_work, h->s));
   }
   for (int l = finest(h); l > h->base; --l) {
     DevLevel& L = h->L[l];

@@ -118,8 +118,10 @@ cudaError_t launch_unpack(const Grid& G, const double* src, double* dst, cudaStr
 cudaError_t launch_shift_copy(const Grid& G, double* f, double* f2, const double* mean_num,
                               double inv_volume, cudaStream_t s);
 cudaError_t launch_fill(double* p, long long n, double v, cudaStream_t s);
+// tau from phi (ghosts, including edges, filled); work holds 3 * grid_elems(G)
+// float64 for the first derivatives.
 cudaError_t launch_lpt2_source(int order, const Grid& G, const double* phi, double invh2,
-                               double* tau, cudaStream_t s);
+                               double* tau, double* work, cudaStream_t s);
 cudaError_t launch_gradient(int order, const Grid& G, const double* phi, double invh, double* dx,
                             double* dy, double* dz, cudaStream_t s);
 

@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kRedBlock)
       if (cov && !r32) continue;
       const long long p = row + k;
       const double fv = __ldg(f + p);
-      const double r = fma(-invh2, lap_h2<ORDER, double>(u, p, sy, sx), fv);
+      const double r = u ? fma(-invh2, lap_h2<ORDER, double>(u, p, sy, sx), fv) : fv;
       if (r32) r32[p] = (float)r;
       if (cov) continue;
       rr = fma(r, r, rr);
@@ -234,45 +234,75 @@ __global__ void __launch_bounds__(256) k_fill(double* __restrict__ p, long long 
   if (t < n) p[t] = v;
 }
 
-// tau = sum_{i<j} (phi_ii phi_jj - phi_ij^2); phi_ii: 1D second difference,
-// phi_ij: composition of the 1D gradients along i and j (reads edge ghosts).
+// First derivatives D_b = G_b phi (Table 1 gradient, times h) for the 2LPT
+// source, on every cell whose b coordinate is interior and whose other two
+// coordinates lie anywhere in the ghost-padded box (the mixed derivatives read
+// D_b up to g cells outside the interior along the other axes).  One thread per
+// (padded x, padded y) row position, looping over padded z.
 template <int ORDER>
 __global__ void __launch_bounds__(128)
-    k_lpt2_source(Grid G, const double* __restrict__ phi, double invh2, double* __restrict__ tau) {
+    k_first_derivs(Grid G, const double* __restrict__ phi, double* __restrict__ dx,
+                   double* __restrict__ dy, double* __restrict__ dz) {
   constexpr int half = ORDER / 2;
-  const long long n = (long long)G.n0 * G.n1 * G.n2;
-  const long long t = blockIdx.x * 128LL + threadIdx.x;
-  if (t >= n) return;
-  const int k = (int)(t % G.n2), j = (int)((t / G.n2) % G.n1), i = (int)(t / ((long long)G.n2 * G.n1));
+  const int g = G.g;
+  const int k = (int)(blockIdx.x * 32 + threadIdx.x) - g;
+  const int j = (int)(blockIdx.y * 4 + threadIdx.y) - g;
+  const int i = (int)blockIdx.z - g;
+  if (k >= G.n2 + g || j >= G.n1 + g) return;
   const long long p = gidx(G, i, j, k);
   const long long st[3] = {(long long)G.Y * G.Zp, (long long)G.Zp, 1};
+  const int crd[3] = {i, j, k};
+  const int n[3] = {G.n0, G.n1, G.n2};
+  double* out[3] = {dx, dy, dz};
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    if (crd[b] < 0 || crd[b] >= n[b]) continue;
+    double acc = 0.0;
+#pragma unroll
+    for (int s = 1; s <= half; ++s)
+      acc = fma(grad_w<ORDER>(s), __ldg(phi + p + s * st[b]) - __ldg(phi + p - s * st[b]), acc);
+    out[b][p] = acc;
+  }
+}
+
+// tau = sum_{i<j} (phi_ii phi_jj - phi_ij^2): phi_ii is the 1D second
+// difference along i, phi_ij = G_i (G_j phi) from the stored first derivatives.
+template <int ORDER>
+__global__ void __launch_bounds__(128)
+    k_lpt2_source(Grid G, const double* __restrict__ phi, const double* __restrict__ dx,
+                  const double* __restrict__ dy, const double* __restrict__ dz, double invh2,
+                  double* __restrict__ tau) {
+  constexpr int half = ORDER / 2;
+  const int k = blockIdx.x * 32 + threadIdx.x;
+  const int j = blockIdx.y * 4 + threadIdx.y;
+  const int i = blockIdx.z;
+  if (k >= G.n2 || j >= G.n1) return;
+  const long long p = gidx(G, i, j, k);
+  const long long st[3] = {(long long)G.Y * G.Zp, (long long)G.Zp, 1};
+  const double c = __ldg(phi + p);
   double d[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    double acc = 0.0;
+    double acc = Lap<ORDER>::w0 * c;
 #pragma unroll
-    for (int s = -half; s <= half; ++s) acc = fma(lap_w<ORDER>(s), __ldg(phi + p + s * st[a]), acc);
+    for (int s = 1; s <= half; ++s)
+      acc = fma(lap_w<ORDER>(s), __ldg(phi + p + s * st[a]) + __ldg(phi + p - s * st[a]), acc);
     d[a] = acc * invh2;
   }
+  // phi_xy = G_x D_y, phi_xz = G_x D_z, phi_yz = G_y D_z
+  const double* src[3] = {dy, dz, dz};
+  const int ax[3] = {0, 0, 1};
   double m[3];
-  const int pa[3] = {0, 0, 1}, pb[3] = {1, 2, 2};
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
     double acc = 0.0;
 #pragma unroll
-    for (int sa = -half; sa <= half; ++sa) {
-      if (sa == 0) continue;
-      double inner = 0.0;
-#pragma unroll
-      for (int sb = -half; sb <= half; ++sb) {
-        if (sb == 0) continue;
-        inner = fma(grad_w<ORDER>(sb), __ldg(phi + p + sa * st[pa[q]] + sb * st[pb[q]]), inner);
-      }
-      acc = fma(grad_w<ORDER>(sa), inner, acc);
-    }
+    for (int s = 1; s <= half; ++s)
+      acc = fma(grad_w<ORDER>(s), __ldg(src[q] + p + s * st[ax[q]]) - __ldg(src[q] + p - s * st[ax[q]]),
+                acc);
     m[q] = acc * invh2;
   }
-  tau[p] = d[0] * d[1] + d[0] * d[2] + d[1] * d[2] - m[0] * m[0] - m[1] * m[1] - m[2] * m[2];
+  tau[p] = fma(d[0], d[1] + d[2], d[1] * d[2]) - fma(m[0], m[0], fma(m[1], m[1], m[2] * m[2]));
 }
 
 template <int ORDER>
@@ -397,13 +427,27 @@ cudaError_t launch_fill(double* p, long long n, double v, cudaStream_t s) {
 }
 
 cudaError_t launch_lpt2_source(int order, const Grid& G, const double* phi, double invh2,
-                               double* tau, cudaStream_t s) {
-  const long long n = (long long)G.n0 * G.n1 * G.n2;
-  const unsigned b = blocks_for(n, 128);
+                               double* tau, double* work, cudaStream_t s) {
+  const long long e = grid_elems(G);
+  double* dx = work;
+  double* dy = work + e;
+  double* dz = work + 2 * e;
+  const dim3 block(32, 4, 1);
+  const dim3 gpad((G.n2 + 2 * G.g + 31) / 32, (G.n1 + 2 * G.g + 3) / 4, G.n0 + 2 * G.g);
+  const dim3 gin((G.n2 + 31) / 32, (G.n1 + 3) / 4, G.n0);
   switch (order) {
-    case 2: k_lpt2_source<2><<<b, 128, 0, s>>>(G, phi, invh2, tau); break;
-    case 4: k_lpt2_source<4><<<b, 128, 0, s>>>(G, phi, invh2, tau); break;
-    case 6: k_lpt2_source<6><<<b, 128, 0, s>>>(G, phi, invh2, tau); break;
+    case 2:
+      k_first_derivs<2><<<gpad, block, 0, s>>>(G, phi, dx, dy, dz);
+      k_lpt2_source<2><<<gin, block, 0, s>>>(G, phi, dx, dy, dz, invh2, tau);
+      break;
+    case 4:
+      k_first_derivs<4><<<gpad, block, 0, s>>>(G, phi, dx, dy, dz);
+      k_lpt2_source<4><<<gin, block, 0, s>>>(G, phi, dx, dy, dz, invh2, tau);
+      break;
+    case 6:
+      k_first_derivs<6><<<gpad, block, 0, s>>>(G, phi, dx, dy, dz);
+      k_lpt2_source<6><<<gin, block, 0, s>>>(G, phi, dx, dy, dz, invh2, tau);
+      break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

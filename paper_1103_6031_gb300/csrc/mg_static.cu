@@ -5,7 +5,8 @@
 // allocator, a plugin that is handed a stream but no allocator, or code that
 // must not risk the implicit device synchronisation of cudaMalloc/cudaFree.
 // This entry point serves them: its working memory (a ghost-padded copy of
-// phi and a padded tau) lives in one file-scope __device__ array that every
+// phi, a padded tau and three padded first-derivative arrays) lives in one
+// file-scope __device__ array that every
 // GPU holds from module load until process exit, so the call itself makes no
 // allocation.  The caller passes only the input phi and the output tau.
 //
@@ -25,8 +26,8 @@
 
 namespace {
 
-// Capacity of the static working array: two padded float64 grids.
-constexpr long long kStaticElems = (6LL << 20) / 8;  // 6 MiB
+// Capacity of the static working array: five padded float64 grids.
+constexpr long long kStaticElems = (16LL << 20) / 8;  // 16 MiB
 static __device__ __align__(256) double g_static_work[kStaticElems];
 
 constexpr int kMaxDevices = 64;
@@ -57,7 +58,7 @@ extern "C" mg_status mg_lpt2_source_periodic_static(const double* phi, double* t
     return MG_EINVAL;
   }
   const mgk::Grid G = mgk::make_grid(n0, n1, n2, g);
-  const long long need = 2 * mgk::grid_elems(G);
+  const long long need = 5 * mgk::grid_elems(G);
   if (need > kStaticElems) {
     char buf[256];
     snprintf(buf, sizeof(buf),
@@ -91,7 +92,9 @@ extern "C" mg_status mg_lpt2_source_periodic_static(const double* phi, double* t
   const double h = box / n0;
   cudaError_t e = mgk::launch_pack(G, phi, phi_pad, 0.0, s);
   if (e == cudaSuccess) e = mgk::launch_ghost_periodic<double>(G, phi_pad, s);
-  if (e == cudaSuccess) e = mgk::launch_lpt2_source(order, G, phi_pad, 1.0 / (h * h), tau_pad, s);
+  if (e == cudaSuccess)
+    e = mgk::launch_lpt2_source(order, G, phi_pad, 1.0 / (h * h), tau_pad,
+                                work + 2 * mgk::grid_elems(G), s);
   if (e == cudaSuccess) e = mgk::launch_unpack(G, tau_pad, tau, s);
   if (e != cudaSuccess) {
     put_msg(err, len, cudaGetErrorString(e));

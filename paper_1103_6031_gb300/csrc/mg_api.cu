@@ -466,11 +466,6 @@ mg_status fill_zero(mg_hierarchy* h, double* p, long long e) {
   return MG_OK;
 }
 
-mg_status fill_zero(mg_hierarchy* h, float* p, long long e) {
-  KL(MG_K_COPY, e, launch_fill_zero(p, e, h->s));
-  return MG_OK;
-}
-
 template <typename T>
 mg_status zero_state(mg_hierarchy* h, int from_level) {
   for (int l = from_level; l <= finest(h); ++l) {
@@ -615,9 +610,26 @@ mg_status fp64_cycle_body(mg_hierarchy* h) {
   return norm_launches(h);
 }
 
+// Correction e = 0 on every level: only the current buffer needs zeros (the
+// smoother writes every interior cell and, on periodic levels, every ghost of
+// the other buffer before it is read), and a zero parent gives zero
+// tangential intermediate values and parent fluxes on every nest.
+mg_status zero_correction(mg_hierarchy* h) {
+  for (int l = 0; l <= finest(h); ++l) {
+    DevLevel& L = h->L[l];
+    L.s.cur = 0;
+    L.s.ghosts_stale = false;
+    CK(cudaMemsetAsync(L.s.u[0], 0, (size_t)grid_elems(L.G) * sizeof(float), h->s));
+    if (L.geo.nest) {
+      CK(cudaMemsetAsync(L.s.inter, 0, (size_t)L.fs.base[6] * sizeof(float), h->s));
+      CK(cudaMemsetAsync(L.s.fc_unc, 0, (size_t)L.fs.ebase[6] * sizeof(float), h->s));
+    }
+  }
+  return MG_OK;
+}
+
 mg_status mixed_outer_body(mg_hierarchy* h) {
-  ST(zero_state<float>(h, 0));
-  for (int l = h->base + 1; l <= finest(h); ++l) ST(tangential<float>(h, l));
+  ST(zero_correction(h));
   for (int m = 0; m < h->cfg.inner_cycles; ++m) ST(vcycle<float>(h, finest(h)));
   for (int l = h->base; l <= finest(h); ++l) {
     DevLevel& L = h->L[l];

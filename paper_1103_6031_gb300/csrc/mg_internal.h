@@ -104,7 +104,6 @@ cudaError_t launch_norm_partial(int order, const Grid& G, const double* u, const
                                 int blocks, float* r32, cudaStream_t s);
 cudaError_t launch_add_correction(const Grid& G, double* u, const float* e, int periodic,
                                   cudaStream_t s);
-cudaError_t launch_fill_zero(float* p, long long n, cudaStream_t s);
 // p[0..n) -= sum[0] * scale, with sum on the device
 cudaError_t launch_sub_mean(double* p, long long n, const double* sum, double scale,
                             cudaStream_t s);

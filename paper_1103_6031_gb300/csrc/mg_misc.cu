@@ -224,11 +224,6 @@ __global__ void __launch_bounds__(256)
   if (t < n) p[t] -= sum[0] * scale;
 }
 
-__global__ void __launch_bounds__(256) k_fill_f32(float* __restrict__ p, long long n) {
-  const long long t = blockIdx.x * 256LL + threadIdx.x;
-  if (t < n) p[t] = 0.0f;
-}
-
 __global__ void __launch_bounds__(256) k_fill(double* __restrict__ p, long long n, double v) {
   const long long t = blockIdx.x * 256LL + threadIdx.x;
   if (t < n) p[t] = v;
@@ -411,12 +406,6 @@ cudaError_t launch_sub_mean(double* p, long long n, const double* sum, double sc
                             cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   k_sub_mean<<<blocks_for(n, 256), 256, 0, s>>>(p, n, sum, scale);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_fill_zero(float* p, long long n, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  k_fill_f32<<<blocks_for(n, 256), 256, 0, s>>>(p, n);
   return cudaGetLastError();
 }
 

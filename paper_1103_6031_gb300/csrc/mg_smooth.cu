@@ -172,8 +172,8 @@ dim3 coarse_grid(Int3 cn, dim3 block) {
 template <typename T>
 cudaError_t launch_smooth_half(int order, const Grid& G, const T* uin, T* uout, const T* f,
                                double a_f, int colour, int periodic, cudaStream_t s) {
-  const int pairs = (G.n2 + 1) / 2;
   dim3 block(kPairX, kRowsY, 1);
+  const int pairs = (G.n2 + 1) / 2;
   dim3 grid((pairs + kPairX - 1) / kPairX, (G.n1 + kRowsY - 1) / kRowsY, G.n0);
   switch (order) {
     case 2: k_smooth_half<2, T><<<grid, block, 0, s>>>(G, uin, uout, f, T(a_f), colour, periodic); break;

@@ -34,6 +34,7 @@ METRIC = "level-cells solved/s to 1e-6 rel. error; % HBM peak; p50/p99 solve lat
 UNIT = "level-cells/s"
 SOLVE_TOL = 1e-7
 SEED = 2
+BATCH_SEED = 1000
 # float32 V-cycles per float64 refinement step in the mixed-precision variant
 MIXED_INNER_CYCLES = 4
 # V-cycles of one full step at SOLVE_TOL on this workload (1LPT + 2LPT), as the
@@ -214,9 +215,79 @@ def run_reference(args):
     return 0
 
 
-def run_ours(args):
+def _batch_delta(job):
+    """Input of one batch member (runs in a spawned worker process)."""
+    i, geom = job
+    import numpy as np
+    from synthetic import make_delta
+    return [np.ascontiguousarray(x) for x in make_delta(geom, BATCH_SEED + i)]
+
+
+def batch_inputs():
+    """The 64-hierarchy batched workload and its inputs, generated by a spawned
+    process pool (before the first CUDA call of this process)."""
+    import multiprocessing as mp
+    from synthetic import config_batch
+    geoms = config_batch()
+    workers = max(1, min(16, os.cpu_count() or 1))
+    with mp.get_context("spawn").Pool(workers) as pool:
+        deltas = pool.map(_batch_delta, list(enumerate(geoms)))
+    return geoms, deltas
+
+
+def batched_measure(pkg, geoms, deltas_np, steps, device):
+    """Hierarchies/s on the batched workload: the float64 solve one hierarchy at a
+    time against the mixed-precision batch (one graph launch per iteration)."""
     import torch
+    deltas = [[torch.from_numpy(x).to(device) for x in d] for d in deltas_np]
+    cells = sum(g.level_cells() for g in geoms)
+    res = {}
+    for name, prec, batched in (("fp64_one_at_a_time", pkg.MG_FP64, False),
+                                ("mixed_batched", pkg.MG_MIXED, True)):
+        kw = dict(tol=SOLVE_TOL, max_cycles=50)
+        if prec == pkg.MG_MIXED:
+            kw.update(precision=prec, inner_cycles=MIXED_INNER_CYCLES)
+        hs = [pkg.Hierarchy(pkg.config_from_geometry(g, **kw)) for g in geoms]
+        if batched:
+            runner = pkg.Batch(hs)
+            outs, _, _ = runner.pipeline(deltas)
+            step = lambda: runner.pipeline(deltas, outs)  # noqa: E731
+        else:
+            outs = [h.pipeline(d)[0] for h, d in zip(hs, deltas)]
+
+            def step():
+                for h, d, o in zip(hs, deltas, outs):
+                    h.pipeline(d, o)
+        step()
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(steps):
+            t0 = time.perf_counter()
+            step()
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        dt = statistics.mean(times)
+        res[name] = {"hierarchies_per_s": len(geoms) / dt, "level_cells_per_s": cells / dt,
+                     "ms_per_batch": dt * 1e3}
+        if batched:
+            runner.close()
+        for h in hs:
+            h.close()
+        del outs
+        torch.cuda.empty_cache()
+    res["workload"] = ("64 hierarchies: base side uniform in {32,48,64,96,128}, 0-3 nests of "
+                       "0.5-1.0 x base side (seed 4), order 6, BBKS z=50, 1LPT+2LPT+displacements, "
+                       "%.1f M level-cells per batch" % (cells / 1e6))
+    res["steps"] = steps
+    res["speedup_mixed_batched_vs_fp64"] = (res["mixed_batched"]["hierarchies_per_s"]
+                                            / res["fp64_one_at_a_time"]["hierarchies_per_s"])
+    return res
+
+
+def run_ours(args):
     world, rank, local = dist_env()
+    batch = batch_inputs() if (not args.profile_run and not args.no_batch) else None
+    import torch
     dist = None
     if world > 1:
         import torch.distributed as tdist
@@ -325,6 +396,10 @@ def run_ours(args):
                  "error_bound": "<= 1e-6 RMS relative vs float64 (tests/test_gpu_parity.py)"}
         hm.close()
 
+    batched = None
+    if batch is not None:
+        batched = batched_measure(pkg, batch[0], batch[1], min(args.steps, 3), device)
+
     if args.profile_run:
         if rank == 0:
             print(json.dumps({"profile_run": True, "value": value, "ms_per_step": ms_per_step,
@@ -381,6 +456,7 @@ def run_ours(args):
             "gpu_launches": launches,
             "clocks": clocks,
             "mixed_precision": mixed,
+            "batched": batched,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h,
                     "ms_per_step": statistics.mean(e2e_ms)},
@@ -404,6 +480,8 @@ def main(argv=None):
                     help="leave out the CPU-oracle baseline")
     ap.add_argument("--profile-run", action="store_true",
                     help="timed steps only: no end-to-end pass, no CPU baseline (for ncu)")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="leave out the 64-hierarchy batched measurement")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                     help="precision of the timed steps of a --profile-run")
     args = ap.parse_args(argv)

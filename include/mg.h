@@ -165,6 +165,32 @@ mg_status mg_lpt2_source_periodic_static(const double* phi, double* tau, int n0,
                                          int n2, double box, int order, void* cuda_stream,
                                          char* err, size_t len);
 
+/* A batch of independent hierarchies solved together (config 4 style: many
+ * small, uneven hierarchies).  Each member keeps its own configuration and
+ * device state; the V-cycles (MG_FP64) or outer iterations (MG_MIXED) of all
+ * members that have not converged are captured into one CUDA graph with one
+ * branch per member and replayed with a single launch per iteration, so the
+ * members' kernels run concurrently.  Results equal each member's results
+ * when solved alone (the same kernels on the same data, no cross-member
+ * arithmetic).  Members must not be used elsewhere while the batch runs. */
+typedef struct mg_batch mg_batch;
+
+mg_status mg_batch_create(mg_hierarchy* const members[], int count, void* cuda_stream,
+                          mg_batch** out);
+mg_status mg_batch_destroy(mg_batch* b);
+
+/* mg_lpt_pipeline for every member: delta[i], phi1[i], ... are member i's
+ * pointer arrays (as for mg_lpt_pipeline); info1/info2 are arrays of count
+ * records (or NULL).  Returns the worst member status; MG_ENOCONV if any member
+ * stopped above its tol. */
+mg_status mg_batch_lpt_pipeline(mg_batch* b, int host_buffers, const double* const* const delta[],
+                                double* const* const phi1[], double* const* const phi2[],
+                                double* const* const disp1[], double* const* const disp2[],
+                                mg_info* info1, mg_info* info2);
+
+/* Message for the last failing batch call ("" if none; NULL-safe). */
+const char* mg_batch_last_error(const mg_batch* b);
+
 /* Kernel families for launch counting and event timing. */
 typedef enum {
   MG_K_SMOOTH = 0,     /* red-black half-sweep                                 */

@@ -19,6 +19,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -498,13 +499,14 @@ mg_status sync_covered(mg_hierarchy* h) {
 // host synchronisation, so it can be captured); ends with the copy of 4
 // doubles to pinned host memory.  In MG_MIXED the residual is also stored
 // (float32) as the correction source.
-mg_status norm_launches(mg_hierarchy* h) {
-  ST(sync_covered(h));
+mg_status norm_launches(mg_hierarchy* h, bool zero_u = false) {
+  if (!zero_u) ST(sync_covered(h));
   for (int l = h->base; l <= finest(h); ++l) {
     DevLevel& L = h->L[l];
-    ST(ghost_fill<double>(h, l, false));
+    if (!zero_u) ST(ghost_fill<double>(h, l, false));
     KL(MG_K_NORM, cells_of(L.G),
-       launch_norm_partial(h->cfg.order, L.G, phi_of(L), L.f, 1.0 / (L.geo.h * L.geo.h),
+       launch_norm_partial(h->cfg.order, L.G, zero_u ? nullptr : phi_of(L), L.f,
+                           1.0 / (L.geo.h * L.geo.h),
                            L.geo.h * L.geo.h * L.geo.h, L.child_lo, L.child_hi,
                            h->partial + 2 * L.partial_off, L.nblocks,
                            h->mixed ? L.s.ffas : nullptr, h->s));
@@ -532,11 +534,6 @@ mg_status norm_read(mg_hierarchy* h, double* rr, double* ff, double* fsum) {
   *ff = h->host_red[1];
   if (fsum) *fsum = h->host_red[2];
   return MG_OK;
-}
-
-mg_status leaf_norms(mg_hierarchy* h, double* rr, double* ff, double* fsum) {
-  ST(norm_launches(h));
-  return norm_read(h, rr, ff, fsum);
 }
 
 void destroy_graph(Graph& g) {
@@ -673,49 +670,57 @@ void record(mg_info& local, double rel) {
   local.cycles++;
 }
 
-mg_status solve_fp64(mg_hierarchy* h, mg_info* info) {
-  ST(remove_source_mean(h));
-  ST(zero_state<double>(h, 0));
-  for (int l = h->base + 1; l <= finest(h); ++l) ST(tangential<double>(h, l));
+// A solve in phases, so that one hierarchy can run alone or as a member of a
+// batch whose iterations are replayed together.
+struct SolveState {
   mg_info local;
-  std::memset(&local, 0, sizeof(local));
   double rel = INFINITY;
-  const bool fixed = !(h->cfg.tol > 0.0);
-  for (int c = 0; c < h->cfg.max_cycles; ++c) {
-    ST(run_body(h, c == 0, fp64_cycle_body));
-    double rr, ff, fs;
-    ST(norm_read(h, &rr, &ff, &fs));
-    if (c == 0) local.source_mean = fs / h->volume;
-    rel = ff > 0.0 ? std::sqrt(rr) / std::sqrt(ff) : std::sqrt(rr);
-    record(local, rel);
-    if (!std::isfinite(rel)) break;
-    if (!fixed && rel <= h->cfg.tol) break;
-  }
-  return finish_info(h, local, rel, info);
+  int c = 0;
+  bool done = false;
+};
+
+// Queues the set-up: composite mean removal, zero solution, tangential caches
+// and, in MG_MIXED, the first residual (the source itself: u = 0).
+mg_status solve_begin(mg_hierarchy* h) {
+  ST(remove_source_mean(h));
+  ST(zero_state<double>(h, h->mixed ? h->base : 0));
+  for (int l = h->base + 1; l <= finest(h); ++l) ST(tangential<double>(h, l));
+  if (h->mixed) ST(norm_launches(h, true));
+  return MG_OK;
 }
 
-mg_status solve_mixed(mg_hierarchy* h, mg_info* info) {
-  ST(remove_source_mean(h));
-  ST(zero_state<double>(h, h->base));
-  for (int l = h->base + 1; l <= finest(h); ++l) ST(tangential<double>(h, l));
-  mg_info local;
-  std::memset(&local, 0, sizeof(local));
-  double rr, ff, fs;
-  // the residual of u = 0 is the source; it becomes the first correction source
-  ST(leaf_norms(h, &rr, &ff, &fs));
-  local.source_mean = fs / h->volume;
-  double rel = ff > 0.0 ? std::sqrt(rr) / std::sqrt(ff) : std::sqrt(rr);
-  const bool fixed = !(h->cfg.tol > 0.0);
-  for (int c = 0; c < h->cfg.max_cycles; ++c) {
-    ST(run_body(h, c == 0, mixed_outer_body));
-    local.inner_cycles += h->cfg.inner_cycles;
+mg_status solve_begin_read(mg_hierarchy* h, SolveState& st) {
+  std::memset(&st.local, 0, sizeof(st.local));
+  st.c = 0;
+  st.done = false;
+  st.rel = INFINITY;
+  if (h->mixed) {
+    double rr, ff, fs;
     ST(norm_read(h, &rr, &ff, &fs));
-    rel = ff > 0.0 ? std::sqrt(rr) / std::sqrt(ff) : std::sqrt(rr);
-    record(local, rel);
-    if (!std::isfinite(rel)) break;
-    if (!fixed && rel <= h->cfg.tol) break;
+    st.local.source_mean = fs / h->volume;
+    st.rel = ff > 0.0 ? std::sqrt(rr) / std::sqrt(ff) : std::sqrt(rr);
   }
-  return finish_info(h, local, rel, info);
+  return MG_OK;
+}
+
+// The launches of one V-cycle (MG_FP64) or one outer iteration (MG_MIXED).
+mg_status solve_body(mg_hierarchy* h) {
+  return h->mixed ? mixed_outer_body(h) : fp64_cycle_body(h);
+}
+
+// Reads the convergence record of the iteration just run.
+mg_status solve_step_read(mg_hierarchy* h, SolveState& st) {
+  double rr, ff, fs;
+  ST(norm_read(h, &rr, &ff, &fs));
+  if (st.c == 0 && !h->mixed) st.local.source_mean = fs / h->volume;
+  if (h->mixed) st.local.inner_cycles += h->cfg.inner_cycles;
+  st.rel = ff > 0.0 ? std::sqrt(rr) / std::sqrt(ff) : std::sqrt(rr);
+  record(st.local, st.rel);
+  st.c++;
+  const bool fixed = !(h->cfg.tol > 0.0);
+  st.done = !std::isfinite(st.rel) || (!fixed && st.rel <= h->cfg.tol) ||
+            st.c >= h->cfg.max_cycles;
+  return MG_OK;
 }
 
 // The periodic problem fixes u only up to a constant.  The float64 V-cycle
@@ -742,12 +747,22 @@ mg_status gauge_zero_base_mean(mg_hierarchy* h) {
   return MG_OK;
 }
 
+mg_status solve_end(mg_hierarchy* h, SolveState& st, mg_info* info) {
+  const mg_status res = finish_info(h, st.local, st.rel, info);
+  if (res != MG_OK && res != MG_ENOCONV) return res;
+  if (h->mixed) ST(gauge_zero_base_mean(h));
+  return res;
+}
+
 mg_status solve_prepared(mg_hierarchy* h, mg_info* info) {
-  if (!h->mixed) return solve_fp64(h, info);
-  const mg_status st = solve_mixed(h, info);
-  if (st != MG_OK && st != MG_ENOCONV) return st;
-  ST(gauge_zero_base_mean(h));
-  return st;
+  SolveState st;
+  ST(solve_begin(h));
+  ST(solve_begin_read(h, st));
+  while (!st.done) {
+    ST(run_body(h, st.c == 0, solve_body));
+    ST(solve_step_read(h, st));
+  }
+  return solve_end(h, st, info);
 }
 
 cudaMemcpy3DParms dense_padded_parms(const DevLevel& L, double* padded, double* dense,
@@ -874,9 +889,272 @@ bool check_ptrs(const void* const* p, int count) {
 
 }  // namespace
 
+// ---- batches ---------------------------------------------------------------------
+//
+// A batch solves independent hierarchies together.  Each member keeps its own
+// work stream; the V-cycles (or outer iterations) of all members that have not
+// converged yet are captured fork-join into one CUDA graph, one branch per
+// member, and replayed with one launch per iteration, so the small kernels of
+// different hierarchies run concurrently.  A member leaves the graph once it
+// has converged; graphs are cached per set of active members.
+
+namespace {
+
+struct BatchGraph {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<mg_stats> delta;  // launch counts each member adds per replay
+};
+
+}  // namespace
+
+struct mg_batch {
+  std::vector<mg_hierarchy*> m;
+  cudaStream_t user_s = nullptr;
+  cudaStream_t s = nullptr;  // capture / replay stream
+  cudaEvent_t ev_in = nullptr, fork = nullptr;
+  std::vector<cudaEvent_t> join;   // recorded inside captures only
+  std::vector<cudaEvent_t> ready;  // member stream -> batch stream ordering before a replay
+  std::map<std::vector<bool>, BatchGraph> graphs;
+  std::string err;
+};
+
+namespace {
+
+mg_status bfail(mg_batch* b, mg_status st, const std::string& msg) {
+  b->err = msg;
+  return st;
+}
+
+#define BCK(expr)                                                                  \
+  do {                                                                             \
+    cudaError_t e_ = (expr);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      return bfail(b, MG_ECUDA, std::string("CUDA error ") + cudaGetErrorString(e_) + \
+                                    " in " #expr);                                 \
+  } while (0)
+
+mg_status member_status(mg_batch* b, int i, mg_status st) {
+  if (st != MG_OK && st != MG_ENOCONV)
+    b->err = "member " + std::to_string(i) + ": " + b->m[i]->err;
+  return st;
+}
+
+mg_status batch_graph(mg_batch* b, const std::vector<bool>& active, BatchGraph** out) {
+  auto it = b->graphs.find(active);
+  if (it != b->graphs.end()) {
+    *out = &it->second;
+    return MG_OK;
+  }
+  BatchGraph g;
+  g.delta.resize(b->m.size());
+  BCK(cudaStreamBeginCapture(b->s, cudaStreamCaptureModeRelaxed));
+  mg_status st = MG_OK;
+  cudaError_t e = cudaEventRecord(b->fork, b->s);
+  for (size_t i = 0; i < b->m.size() && st == MG_OK && e == cudaSuccess; ++i) {
+    if (!active[i]) continue;
+    mg_hierarchy* h = b->m[i];
+    e = cudaStreamWaitEvent(h->s, b->fork, 0);
+    if (e != cudaSuccess) break;
+    const mg_stats snap = h->stats;
+    const unsigned keep = h->active_mask;
+    h->active_mask = 0;
+    st = solve_body(h);
+    h->active_mask = keep;
+    for (int f = 0; f < MG_K_FAMILIES; ++f) {
+      g.delta[i].launches[f] = h->stats.launches[f] - snap.launches[f];
+      g.delta[i].cells[f] = h->stats.cells[f] - snap.cells[f];
+    }
+    h->stats = snap;
+    if (st != MG_OK) {
+      member_status(b, (int)i, st);
+      break;
+    }
+    e = cudaEventRecord(b->join[i], h->s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->s, b->join[i], 0);
+  }
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(b->s, &graph);
+  if (st != MG_OK || e != cudaSuccess || ee != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    if (st != MG_OK) return st;
+    BCK(e != cudaSuccess ? e : ee);
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  BCK(ei);
+  auto res = b->graphs.emplace(active, g);
+  *out = &res.first->second;
+  return MG_OK;
+}
+
+// Solves every member; f of every member holds its source.
+mg_status batch_solve(mg_batch* b, mg_info* infos) {
+  const size_t n = b->m.size();
+  std::vector<SolveState> st(n);
+  for (size_t i = 0; i < n; ++i) {
+    mg_status r = solve_begin(b->m[i]);
+    if (r != MG_OK) return member_status(b, (int)i, r);
+  }
+  for (size_t i = 0; i < n; ++i) {
+    mg_status r = solve_begin_read(b->m[i], st[i]);
+    if (r != MG_OK) return member_status(b, (int)i, r);
+  }
+  for (;;) {
+    std::vector<bool> active(n);
+    bool any = false;
+    for (size_t i = 0; i < n; ++i) {
+      active[i] = !st[i].done;
+      any = any || active[i];
+    }
+    if (!any) break;
+    BatchGraph* g = nullptr;
+    ST(batch_graph(b, active, &g));
+    // the replay runs on the batch stream: order it after everything already
+    // queued on the active members' own streams (set-up, tau, previous work)
+    for (size_t i = 0; i < n; ++i) {
+      if (!active[i]) continue;
+      BCK(cudaEventRecord(b->ready[i], b->m[i]->s));
+      BCK(cudaStreamWaitEvent(b->s, b->ready[i], 0));
+    }
+    BCK(cudaGraphLaunch(g->exec, b->s));
+    BCK(cudaStreamSynchronize(b->s));
+    for (size_t i = 0; i < n; ++i) {
+      if (!active[i]) continue;
+      mg_hierarchy* h = b->m[i];
+      for (int f = 0; f < MG_K_FAMILIES; ++f) {
+        h->stats.launches[f] += g->delta[i].launches[f];
+        h->stats.cells[f] += g->delta[i].cells[f];
+      }
+      h->replayed = nullptr;
+      mg_status r = solve_step_read(h, st[i]);
+      if (r != MG_OK) return member_status(b, (int)i, r);
+    }
+  }
+  mg_status worst = MG_OK;
+  for (size_t i = 0; i < n; ++i) {
+    mg_status r = solve_end(b->m[i], st[i], infos ? &infos[i] : nullptr);
+    if (r != MG_OK && r != MG_ENOCONV) return member_status(b, (int)i, r);
+    if (r == MG_ENOCONV) worst = MG_ENOCONV;
+  }
+  return worst;
+}
+
+mg_status batch_pipeline(mg_batch* b, bool host, const double* const* const delta[],
+                         double* const* const phi1[], double* const* const phi2[],
+                         double* const* const disp1[], double* const* const disp2[],
+                         mg_info* info1, mg_info* info2) {
+  const size_t n = b->m.size();
+  for (size_t i = 0; i < n; ++i) {
+    mg_hierarchy* h = b->m[i];
+    for (int l = h->base; l <= finest(h); ++l) {
+      mg_status r = load_leaf(h, l, delta[i][l - h->base], h->L[l].f, host);
+      if (r != MG_OK) return member_status(b, (int)i, r);
+    }
+  }
+  mg_status st1 = batch_solve(b, info1);
+  if (st1 != MG_OK && st1 != MG_ENOCONV) return st1;
+  for (size_t i = 0; i < n; ++i) {
+    mg_hierarchy* h = b->m[i];
+    mg_status r = MG_OK;
+    if (phi1 && phi1[i])
+      for (int l = h->base; l <= finest(h) && r == MG_OK; ++l)
+        if (phi1[i][l - h->base]) r = store_leaf(h, l, phi_of(h->L[l]), phi1[i][l - h->base], host);
+    if (r == MG_OK && disp1 && disp1[i]) r = gradient_out(h, disp1[i], host);
+    if (r == MG_OK) r = tau_into_f(h);
+    if (r != MG_OK) return member_status(b, (int)i, r);
+  }
+  mg_status st2 = batch_solve(b, info2);
+  if (st2 != MG_OK && st2 != MG_ENOCONV) return st2;
+  for (size_t i = 0; i < n; ++i) {
+    mg_hierarchy* h = b->m[i];
+    mg_status r = MG_OK;
+    if (phi2 && phi2[i])
+      for (int l = h->base; l <= finest(h) && r == MG_OK; ++l)
+        if (phi2[i][l - h->base]) r = store_leaf(h, l, phi_of(h->L[l]), phi2[i][l - h->base], host);
+    if (r == MG_OK && disp2 && disp2[i]) r = gradient_out(h, disp2[i], host);
+    if (r != MG_OK) return member_status(b, (int)i, r);
+  }
+  for (size_t i = 0; i < n; ++i) BCK(cudaStreamSynchronize(b->m[i]->s));
+  return st1 != MG_OK ? st1 : st2;
+}
+
+}  // namespace
+
 // ---- C ABI -------------------------------------------------------------------
 
 extern "C" {
+
+mg_status mg_batch_create(mg_hierarchy* const members[], int count, void* cuda_stream,
+                          mg_batch** out) {
+  if (!out || !members || count < 1 || count > 4096) return MG_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < count; ++i) {
+    if (!members[i]) return MG_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (members[j] == members[i]) return MG_EINVAL;
+  }
+  mg_batch* b = new mg_batch();
+  b->m.assign(members, members + count);
+  b->user_s = (cudaStream_t)cuda_stream;
+  b->join.assign(count, nullptr);
+  b->ready.assign(count, nullptr);
+  bool ok = cudaStreamCreateWithFlags(&b->s, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; i < count && ok; ++i)
+    ok = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->ready[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    mg_batch_destroy(b);
+    return MG_ECUDA;
+  }
+  *out = b;
+  return MG_OK;
+}
+
+mg_status mg_batch_destroy(mg_batch* b) {
+  if (!b) return MG_OK;
+  if (b->s) cudaStreamSynchronize(b->s);
+  for (auto& kv : b->graphs)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  for (cudaEvent_t e : b->join)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : b->ready)
+    if (e) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->s) cudaStreamDestroy(b->s);
+  delete b;
+  return MG_OK;
+}
+
+const char* mg_batch_last_error(const mg_batch* b) { return b ? b->err.c_str() : ""; }
+
+mg_status mg_batch_lpt_pipeline(mg_batch* b, int host_buffers, const double* const* const delta[],
+                                double* const* const phi1[], double* const* const phi2[],
+                                double* const* const disp1[], double* const* const disp2[],
+                                mg_info* info1, mg_info* info2) {
+  if (!b || !delta) return MG_EINVAL;
+  const bool host = host_buffers != 0;
+  for (size_t i = 0; i < b->m.size(); ++i) {
+    mg_hierarchy* h = b->m[i];
+    const int nleaf = n_leaf(h);
+    if (!check_ptrs((const void* const*)delta[i], nleaf))
+      return bfail(b, MG_EINVAL, "member " + std::to_string(i) + ": delta pointers missing");
+    if (!host && (!disp1 || !disp2 || !check_ptrs((const void* const*)disp1[i], 3 * nleaf) ||
+                  !check_ptrs((const void* const*)disp2[i], 3 * nleaf)))
+      return bfail(b, MG_EINVAL, "member " + std::to_string(i) + ": device displacement outputs missing");
+  }
+  BCK(cudaEventRecord(b->ev_in, b->user_s));
+  for (mg_hierarchy* h : b->m) BCK(cudaStreamWaitEvent(h->s, b->ev_in, 0));
+  const mg_status st = batch_pipeline(b, host, delta, phi1, phi2, disp1, disp2, info1, info2);
+  for (mg_hierarchy* h : b->m) {
+    BCK(cudaEventRecord(h->ev_out, h->s));
+    BCK(cudaStreamWaitEvent(b->user_s, h->ev_out, 0));
+  }
+  return st;
+}
+
 
 void mg_config_default(mg_config* cfg) {
   if (!cfg) return;

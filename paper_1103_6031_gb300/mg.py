@@ -112,6 +112,12 @@ def load_library(path=None):
                                            ctypes.POINTER(MGInfo), ctypes.POINTER(MGInfo)]),
         "mg_set_profiling": (ctypes.c_int, [vp, ctypes.c_uint]),
         "mg_get_stats": (ctypes.c_int, [vp, ctypes.POINTER(MGStats), ctypes.c_int]),
+        "mg_batch_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, vp, ctypes.POINTER(vp)]),
+        "mg_batch_destroy": (ctypes.c_int, [vp]),
+        "mg_batch_lpt_pipeline": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                                 ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                                 ctypes.POINTER(MGInfo), ctypes.POINTER(MGInfo)]),
+        "mg_batch_last_error": (ctypes.c_char_p, [vp]),
         "mg_last_error": (ctypes.c_char_p, [vp]),
         "mg_version": (ctypes.c_char_p, []),
     }
@@ -289,6 +295,69 @@ class Hierarchy:
         if getattr(self, "h", None):
             self.lib.mg_hierarchy_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent hierarchies solved together: each iteration of all members
+    that have not converged is one CUDA-graph launch (one branch per member)."""
+
+    def __init__(self, hierarchies, stream=None):
+        import torch
+        self._torch = torch
+        self.members = list(hierarchies)
+        self.lib = load_library()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        arr = (ctypes.c_void_p * len(self.members))(*[m.h.value for m in self.members])
+        handle = ctypes.c_void_p()
+        st = self.lib.mg_batch_create(arr, len(self.members), ctypes.c_void_p(self.stream.cuda_stream),
+                                      ctypes.byref(handle))
+        if st != 0:
+            raise MGError(st, "mg_batch_create")
+        self.b = handle
+
+    def pipeline(self, deltas, outputs=None, host=False, allow_noconv=False):
+        """deltas[i]: member i's per-level inputs; returns (outputs, infos1, infos2),
+        outputs[i] a dict like Hierarchy.pipeline's."""
+        n = len(self.members)
+        if outputs is None:
+            outputs = []
+            for m in self.members:
+                mk = (lambda s: self._torch.empty(s, dtype=self._torch.float64, pin_memory=True)) if host \
+                    else m._empty
+                outputs.append({"phi1": [mk(s) for s in m.shapes], "phi2": [mk(s) for s in m.shapes],
+                                "disp1": [mk(s) for s in m.shapes for _ in range(3)],
+                                "disp2": [mk(s) for s in m.shapes for _ in range(3)]})
+        keep = []
+
+        def table(key):
+            rows = (ctypes.c_void_p * n)()
+            for i, m in enumerate(self.members):
+                shapes = m.shapes if key in ("delta", "phi1", "phi2") else [s for s in m.shapes for _ in range(3)]
+                src = deltas[i] if key == "delta" else outputs[i][key]
+                row = _ptrs(src, shapes, host)
+                keep.append(row)
+                rows[i] = ctypes.cast(row, ctypes.c_void_p)
+            return rows
+
+        i1 = (MGInfo * n)()
+        i2 = (MGInfo * n)()
+        st = self.lib.mg_batch_lpt_pipeline(self.b, 1 if host else 0, table("delta"), table("phi1"),
+                                            table("phi2"), table("disp1"), table("disp2"), i1, i2)
+        if not (st == 0 or (allow_noconv and st == 3)):
+            msg = self.lib.mg_batch_last_error(self.b)
+            raise MGError(st, "mg_batch_lpt_pipeline: " + (msg.decode() if msg else ""))
+        return outputs, [x.as_dict() for x in i1], [x.as_dict() for x in i2]
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.mg_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:

@@ -35,6 +35,7 @@ UNIT = "level-cells/s"
 SOLVE_TOL = 1e-7
 SEED = 2
 BATCH_SEED = 1000
+SERVE_SEED = 5
 # float32 V-cycles per float64 refinement step in the mixed-precision variant
 MIXED_INNER_CYCLES = 4
 # V-cycles of one full step at SOLVE_TOL on this workload (1LPT + 2LPT), as the
@@ -223,16 +224,70 @@ def _batch_delta(job):
     return [np.ascontiguousarray(x) for x in make_delta(geom, BATCH_SEED + i)]
 
 
-def batch_inputs():
-    """The 64-hierarchy batched workload and its inputs, generated by a spawned
-    process pool (before the first CUDA call of this process)."""
+def serve_large_geometry(side):
+    """Large request class of the serving mix: side^3 base + 3 nests of side^3."""
+    from synthetic import config_deep_zoom
+    return config_deep_zoom(seed=SERVE_SEED, base=side, nest=side, levels=3,
+                            jitter=max(1, side // 8))
+
+
+def batch_inputs(large_side=None):
+    """The 64-hierarchy batched workload (and, if asked, the large serving
+    class) with inputs generated by a spawned process pool, before the first
+    CUDA call of this process."""
     import multiprocessing as mp
     from synthetic import config_batch
     geoms = config_batch()
+    jobs = list(enumerate(geoms))
+    if large_side:
+        jobs.append((len(geoms), serve_large_geometry(large_side)))
     workers = max(1, min(16, os.cpu_count() or 1))
     with mp.get_context("spawn").Pool(workers) as pool:
-        deltas = pool.map(_batch_delta, list(enumerate(geoms)))
-    return geoms, deltas
+        deltas = pool.map(_batch_delta, jobs)
+    large = (jobs[-1][1], deltas[-1]) if large_side else None
+    return geoms, deltas[:len(geoms)], large
+
+
+def serving_measure(pkg, geoms, deltas_np, large, seconds, rate, workers):
+    """Open-loop Poisson arrivals (mean `rate`/s for `seconds`): 90% draws from the
+    batched workload's hierarchies, 10% the large class; mixed precision, host
+    buffers in and out, admission by HBM budget, device-resident hierarchies."""
+    import numpy as np
+    import torch
+    from paper_1103_6031_gb300 import serve
+    rng = np.random.Generator(np.random.PCG64(SERVE_SEED))
+    pinned = [[torch.from_numpy(x).pin_memory() for x in d] for d in deltas_np]
+    large_in = [torch.from_numpy(x).pin_memory() for x in large[1]]
+    kw = dict(tol=SOLVE_TOL, max_cycles=50, precision=pkg.MG_MIXED, inner_cycles=MIXED_INNER_CYCLES)
+    cfg_small = [pkg.config_from_geometry(g, **kw) for g in geoms]
+    cfg_large = pkg.config_from_geometry(large[0], **kw)
+    n = int(seconds * rate)
+    reqs, cells = [], 0
+    for k in range(n):
+        if rng.uniform() < 0.1:
+            reqs.append(serve.Request(k, cfg_large, large_in))
+            cells += large[0].level_cells()
+        else:
+            i = int(rng.integers(len(geoms)))
+            reqs.append(serve.Request(k, cfg_small[i], pinned[i]))
+            cells += geoms[i].level_cells()
+    server = serve.Server(workers=workers, hbm_budget=64 << 30, keep_outputs=False)
+    wall = serve.run_open_loop(server, reqs, rate, seed=SERVE_SEED)
+    errors = [r for r in reqs if r.error is not None]
+    stats = serve.latency_stats(reqs)
+    out = {"offered_rate_per_s": rate, "requests": n, "seconds_of_arrivals": seconds,
+           "completed_per_s": n / wall, "level_cells_per_s": cells / wall,
+           "latency_ms": {"p50": stats["p50_ms"], "p99": stats["p99_ms"], "mean": stats["mean_ms"],
+                          "max": stats["max_ms"]},
+           "workers": workers, "peak_inflight": server.peak_inflight,
+           "peak_resident_gb": server.admission.peak / 2 ** 30,
+           "evictions": server.admission.evictions, "errors": len(errors),
+           "mix": "90%% draws from the 64 batched hierarchies, 10%% %d^3 base + 3 nests of %d^3 "
+                  "(%.1f M level-cells); mixed precision; pinned host buffers in and out; "
+                  "latency from arrival to results in host memory" % (
+                      large[0].base_n[0], large[0].base_n[0], large[0].level_cells() / 1e6)}
+    server.close()
+    return out
 
 
 def batched_measure(pkg, geoms, deltas_np, steps, device):
@@ -275,18 +330,47 @@ def batched_measure(pkg, geoms, deltas_np, steps, device):
             h.close()
         del outs
         torch.cuda.empty_cache()
+    # the same batch with the schedule and tile the autotuner picks per size class
+    from paper_1103_6031_gb300 import autotune
+    t0 = time.perf_counter()
+    best = autotune.tune_batch(geoms, deltas, SOLVE_TOL)
+    tune_s = time.perf_counter() - t0
+    hs = [pkg.Hierarchy(c) for c in autotune.batch_configs(geoms, best, SOLVE_TOL)]
+    runner = pkg.Batch(hs)
+    outs, _, _ = runner.pipeline(deltas)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        runner.pipeline(deltas, outs)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    dt = statistics.mean(times)
+    res["mixed_batched_tuned"] = {"hierarchies_per_s": len(geoms) / dt, "level_cells_per_s": cells / dt,
+                                  "ms_per_batch": dt * 1e3, "tuning_s": tune_s,
+                                  "schedule": {k: {"inner_cycles": v[0], "nu1": v[1], "nu2": v[2],
+                                                   "tile_rows": v[3]} for k, v in best.items()}}
+    runner.close()
+    for h in hs:
+        h.close()
+    del outs
+    torch.cuda.empty_cache()
     res["workload"] = ("64 hierarchies: base side uniform in {32,48,64,96,128}, 0-3 nests of "
                        "0.5-1.0 x base side (seed 4), order 6, BBKS z=50, 1LPT+2LPT+displacements, "
                        "%.1f M level-cells per batch" % (cells / 1e6))
     res["steps"] = steps
     res["speedup_mixed_batched_vs_fp64"] = (res["mixed_batched"]["hierarchies_per_s"]
                                             / res["fp64_one_at_a_time"]["hierarchies_per_s"])
+    res["speedup_tuned_vs_fp64"] = (res["mixed_batched_tuned"]["hierarchies_per_s"]
+                                    / res["fp64_one_at_a_time"]["hierarchies_per_s"])
     return res
 
 
 def run_ours(args):
     world, rank, local = dist_env()
-    batch = batch_inputs() if (not args.profile_run and not args.no_batch) else None
+    batch = None
+    if not args.profile_run and not args.no_batch:
+        batch = batch_inputs(args.serve_large_side if args.serve_seconds > 0 else None)
     import torch
     dist = None
     if world > 1:
@@ -397,8 +481,12 @@ def run_ours(args):
         hm.close()
 
     batched = None
+    serving = None
     if batch is not None:
         batched = batched_measure(pkg, batch[0], batch[1], min(args.steps, 3), device)
+        if args.serve_seconds > 0 and world == 1:
+            serving = serving_measure(pkg, batch[0], batch[1], batch[2], args.serve_seconds,
+                                      args.serve_rate, args.serve_workers)
 
     if args.profile_run:
         if rank == 0:
@@ -457,6 +545,7 @@ def run_ours(args):
             "clocks": clocks,
             "mixed_precision": mixed,
             "batched": batched,
+            "serving": serving,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h,
                     "ms_per_step": statistics.mean(e2e_ms)},
@@ -481,7 +570,13 @@ def main(argv=None):
     ap.add_argument("--profile-run", action="store_true",
                     help="timed steps only: no end-to-end pass, no CPU baseline (for ncu)")
     ap.add_argument("--no-batch", action="store_true",
-                    help="leave out the 64-hierarchy batched measurement")
+                    help="leave out the 64-hierarchy batched and the serving measurements")
+    ap.add_argument("--serve-seconds", type=float, default=5.0,
+                    help="seconds of open-loop arrivals in the serving measurement (0: none)")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="mean arrivals per second")
+    ap.add_argument("--serve-workers", type=int, default=6, help="concurrent requests at most")
+    ap.add_argument("--serve-large-side", type=int, default=128,
+                    help="side of the large request class (base and 3 nests); 256 is full size")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                     help="precision of the timed steps of a --profile-run")
     args = ap.parse_args(argv)

@@ -83,6 +83,8 @@ typedef struct {
                                        /* refinement iterations)                        */
   int inner_cycles;                    /* MG_MIXED: float32 V-cycles per outer iteration */
   int flags;                           /* MG_FLAG_* bits; 0 = defaults                  */
+  int tile_rows;                       /* smoother block: 32 z-pairs x tile_rows y rows  */
+                                       /* (1, 2, 4, 8; 0 = 4)                            */
   double tol;                          /* stop when leaf |r| / leaf |f| <= tol          */
   void* (*dev_alloc)(size_t bytes, void* ctx);
   void (*dev_free)(void* ptr, void* ctx);
@@ -98,7 +100,8 @@ typedef struct {
 } mg_info;
 
 /* Fill *cfg with defaults: order 2, FP64, nu1 = nu2 = 2, max_cycles 50,
- * inner_cycles 2, tol 1e-10, box 1, no nests, NULL allocator.  Host only. */
+ * inner_cycles 2, tile_rows 4, tol 1e-10, box 1, no nests, NULL allocator.
+ * Host only. */
 void mg_config_default(mg_config* cfg);
 
 /* Check the geometry and parameters without touching a GPU.  On failure
@@ -119,6 +122,10 @@ mg_status mg_hierarchy_create(const mg_config* cfg, void* cuda_stream, mg_hierar
 
 /* Free the working state (NULL-safe). */
 mg_status mg_hierarchy_destroy(mg_hierarchy* h);
+
+/* Change the caller's stream that later calls are ordered against (a server
+ * hands a resident hierarchy to whichever worker stream serves a request). */
+mg_status mg_set_stream(mg_hierarchy* h, void* cuda_stream);
 
 /* 1LPT potential (Sec. 3.1.1, 3.2-3.3): solve L phi = delta - <delta>.
  * delta[l], phi[l]: n_levels device pointers, dense float64 per level.

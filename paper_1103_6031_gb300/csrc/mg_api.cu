@@ -354,6 +354,10 @@ bool validate(const mg_config* cfg, char* msg, size_t len, Plan* plan) {
     if (msg && len) snprintf(msg, len, "nu1, nu2 must be in [0, 16] with nu1 + nu2 >= 1");
     return false;
   }
+  if (cfg->tile_rows < 0 || cfg->tile_rows > 8) {
+    if (msg && len) snprintf(msg, len, "tile_rows must be in [0, 8]");
+    return false;
+  }
   if (cfg->max_cycles < 1 || cfg->max_cycles > 1000) {
     if (msg && len) snprintf(msg, len, "max_cycles must be in [1, 1000]");
     return false;
@@ -419,7 +423,7 @@ mg_status half_sweep(mg_hierarchy* h, int l, int colour) {
   const double a_f = L.geo.h * L.geo.h / centre_weight(h->cfg.order);
   KL(MG_K_SMOOTH, (cells_of(L.G) + 1) / 2,
      launch_smooth_half<T>(h->cfg.order, L.G, b.u[b.cur], b.u[1 - b.cur], b.ffas, a_f, colour,
-                           L.periodic ? 1 : 0, h->s));
+                           L.periodic ? 1 : 0, h->cfg.tile_rows > 0 ? h->cfg.tile_rows : 4, h->s));
   b.cur ^= 1;
   return MG_OK;
 }
@@ -1168,6 +1172,7 @@ void mg_config_default(mg_config* cfg) {
   cfg->nu2 = 2;
   cfg->max_cycles = 50;
   cfg->inner_cycles = 2;
+  cfg->tile_rows = 4;
   cfg->tol = 1e-10;
 }
 
@@ -1189,6 +1194,12 @@ int mg_total_levels(const mg_config* cfg) {
 }
 
 const char* mg_version(void) { return "mgic-gb300 0.2 (sm_103a)"; }
+
+mg_status mg_set_stream(mg_hierarchy* h, void* cuda_stream) {
+  if (!h) return MG_EINVAL;
+  h->user_s = (cudaStream_t)cuda_stream;
+  return MG_OK;
+}
 
 mg_status mg_set_profiling(mg_hierarchy* h, unsigned mask) {
   if (!h) return MG_EINVAL;

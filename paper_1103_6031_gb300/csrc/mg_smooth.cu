@@ -15,15 +15,14 @@ namespace mgk {
 
 namespace {
 
-constexpr int kPairX = 32;  // z-pairs per block row
-constexpr int kRowsY = 4;   // y rows per block
+constexpr int kPairX = 32;  // z-pairs per block row; blockDim.y = rows (1..8)
 
 template <int ORDER, typename T>
-__global__ void __launch_bounds__(kPairX* kRowsY)
+__global__ void __launch_bounds__(kPairX * 8)
     k_smooth_half(Grid G, const T* __restrict__ uin, T* __restrict__ uout,
                   const T* __restrict__ f, T a_f, int colour, int periodic) {
   const int t = blockIdx.x * kPairX + threadIdx.x;
-  const int j = blockIdx.y * kRowsY + threadIdx.y;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int i = blockIdx.z;
   const int k0 = 2 * t;
   if (j >= G.n1 || k0 >= G.n2) return;
@@ -171,10 +170,11 @@ dim3 coarse_grid(Int3 cn, dim3 block) {
 
 template <typename T>
 cudaError_t launch_smooth_half(int order, const Grid& G, const T* uin, T* uout, const T* f,
-                               double a_f, int colour, int periodic, cudaStream_t s) {
-  dim3 block(kPairX, kRowsY, 1);
+                               double a_f, int colour, int periodic, int rows, cudaStream_t s) {
+  if (rows < 1 || rows > 8) return cudaErrorInvalidValue;
+  dim3 block(kPairX, rows, 1);
   const int pairs = (G.n2 + 1) / 2;
-  dim3 grid((pairs + kPairX - 1) / kPairX, (G.n1 + kRowsY - 1) / kRowsY, G.n0);
+  dim3 grid((pairs + kPairX - 1) / kPairX, (G.n1 + rows - 1) / rows, G.n0);
   switch (order) {
     case 2: k_smooth_half<2, T><<<grid, block, 0, s>>>(G, uin, uout, f, T(a_f), colour, periodic); break;
     case 4: k_smooth_half<4, T><<<grid, block, 0, s>>>(G, uin, uout, f, T(a_f), colour, periodic); break;
@@ -234,7 +234,7 @@ cudaError_t launch_restrict_u(const Grid& F, const T* u, const Grid& P, T* pu, I
 
 #define MGK_INSTANTIATE(T)                                                                     \
   template cudaError_t launch_smooth_half<T>(int, const Grid&, const T*, T*, const T*, double, \
-                                             int, int, cudaStream_t);                          \
+                                             int, int, int, cudaStream_t);                     \
   template cudaError_t launch_residual_restrict<T>(int, const Grid&, const T*, const T*,       \
                                                    double, const Grid&, T*, T*, T*, Int3,      \
                                                    Int3, int, cudaStream_t);                   \

@@ -36,6 +36,7 @@ class MGConfig(ctypes.Structure):
         ("max_cycles", ctypes.c_int),
         ("inner_cycles", ctypes.c_int),
         ("flags", ctypes.c_int),
+        ("tile_rows", ctypes.c_int),
         ("tol", ctypes.c_double),
         ("dev_alloc", _ALLOC_FN),
         ("dev_free", _FREE_FN),
@@ -110,6 +111,7 @@ def load_library(path=None):
         "mg_lpt2_source": (ctypes.c_int, [vp, pp, pp]),
         "mg_lpt_pipeline": (ctypes.c_int, [vp, ctypes.c_int, pp, pp, pp, pp, pp,
                                            ctypes.POINTER(MGInfo), ctypes.POINTER(MGInfo)]),
+        "mg_set_stream": (ctypes.c_int, [vp, vp]),
         "mg_set_profiling": (ctypes.c_int, [vp, ctypes.c_uint]),
         "mg_get_stats": (ctypes.c_int, [vp, ctypes.POINTER(MGStats), ctypes.c_int]),
         "mg_batch_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, vp, ctypes.POINTER(vp)]),
@@ -131,7 +133,7 @@ def load_library(path=None):
 
 
 def make_config(base_n, box, order, nests=(), precision=MG_FP64, nu1=2, nu2=2, max_cycles=50,
-                tol=1e-10, inner_cycles=2, graphs=True):
+                tol=1e-10, inner_cycles=2, graphs=True, tile_rows=4):
     """MGConfig from plain values; nests = [(n3, off3), ...] (off in parent cells)."""
     lib = load_library()
     cfg = MGConfig()
@@ -149,6 +151,7 @@ def make_config(base_n, box, order, nests=(), precision=MG_FP64, nu1=2, nu2=2, m
     cfg.nu1, cfg.nu2, cfg.max_cycles, cfg.tol = int(nu1), int(nu2), int(max_cycles), float(tol)
     cfg.inner_cycles = int(inner_cycles)
     cfg.flags = 0 if graphs else MG_FLAG_NO_GRAPHS
+    cfg.tile_rows = int(tile_rows)
     return cfg
 
 
@@ -278,6 +281,11 @@ class Hierarchy:
                                       ctypes.byref(i1), ctypes.byref(i2))
         self._check(st, "mg_lpt_pipeline", allow_noconv)
         return outputs, i1.as_dict(), i2.as_dict()
+
+    def set_stream(self, stream):
+        """Order later calls against `stream` (a torch.cuda.Stream)."""
+        self._check(self.lib.mg_set_stream(self.h, ctypes.c_void_p(stream.cuda_stream)), "mg_set_stream")
+        self.stream = stream
 
     def set_profiling(self, families=()):
         """Time every launch of the named kernel families with CUDA events."""

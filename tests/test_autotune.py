@@ -1,0 +1,56 @@
+"""Autotuner host logic (CPU) and one tuning run on the GPU."""
+
+import numpy as np
+import pytest
+
+from synthetic import Geometry, config_batch, make_delta, small_zoom
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1103_6031_gb300 as p
+    return p
+
+
+def test_size_classes_and_representatives(pkg):
+    from paper_1103_6031_gb300 import autotune
+    geoms = config_batch()
+    classes = [autotune.size_class(g) for g in geoms]
+    assert set(classes) <= {"xs", "s", "m", "l"}
+    reps = autotune.representatives(geoms)
+    for name, i in reps.items():
+        members = sorted((g.level_cells() for g, c in zip(geoms, classes) if c == name))
+        assert geoms[i].level_cells() == members[len(members) // 2]
+        assert autotune.size_class(geoms[i]) == name
+
+
+def test_every_candidate_is_a_valid_config(pkg):
+    from paper_1103_6031_gb300 import autotune
+    geom = config_batch()[0]
+    for params in autotune.DEFAULT_SPACE:
+        cfg = autotune.config(geom, params, 1e-7)
+        assert pkg.validate(cfg)[0] == 0, params
+
+
+@pytest.mark.gpu
+def test_tuned_schedule_converges_and_is_fastest(pkg):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1103_6031_gb300 import autotune
+    geom = small_zoom(32, ((32, 8),), order=6, box=50.0)
+    d = [torch.from_numpy(x).cuda() for x in make_delta(geom, 3)]
+    space = [(2, 2, 2, 4), (3, 1, 1, 2), (4, 2, 1, 8)]
+    best, table = autotune.tune(geom, d, 1e-8, space=space, reps=2)
+    assert best in space and table[best] == min(t for t in table.values() if t is not None)
+    h = pkg.Hierarchy(autotune.config(geom, best, 1e-8))
+    ref = pkg.Hierarchy(pkg.config_from_geometry(geom, tol=1e-12))
+    a, i1, i2 = h.pipeline(d)
+    b, _, _ = ref.pipeline(d)
+    assert i1["rel_residual"] <= 1e-8 and i2["rel_residual"] <= 1e-8
+    for key in ("phi1", "phi2", "disp1", "disp2"):
+        for x, y in zip(a[key], b[key]):
+            err = float(torch.sqrt(((x - y) ** 2).sum() / (y ** 2).sum()))
+            assert err <= 1e-6, key

@@ -241,3 +241,30 @@ def test_mixed_precision_bench_workload(lib):
     for key in ("phi1", "phi2", "disp1", "disp2"):
         for x, y in zip(a[key], b[key]):
             assert rel(x, y.cpu().numpy()) <= 1e-6, key
+
+
+def test_deep_zoom_full_size(lib):
+    """128^3 base + 4 nests of 128^3 (jittered offsets): float64 matches the oracle
+    element by element at a matched cycle count; the mixed-precision step stays
+    within 1e-6 of tightly converged float64 solves."""
+    from synthetic import config_deep_zoom
+    geom = config_deep_zoom()
+    deltas = make_delta(geom, 3)
+    ref, rinfo = oracle_solve(geom, deltas, tol=0.0, cycles=2)
+    h = hier(lib, geom, tol=0.0, max_cycles=2)
+    phis, info = h.solve_1lpt(to_dev(deltas))
+    for l in range(geom.n_levels):
+        assert rel(phis[l], ref[l]) < TOL
+    np.testing.assert_allclose(info["history"], rinfo["history"], rtol=1e-6, atol=1e-14)
+    h.close()
+    d = to_dev(deltas)
+    tight = hier(lib, geom, tol=1e-12)
+    b, t1, t2 = tight.pipeline(d)
+    hist = t1["history"]
+    # >= 10x per cycle until the float64 rounding floor of the composite residual
+    assert all(x / y >= 10.0 for x, y in zip(hist[:-1], hist[1:]) if y > 1e-10), hist
+    mixed = hier(lib, geom, tol=1e-7, precision=lib.MG_MIXED, inner_cycles=4)
+    a, _, _ = mixed.pipeline(d)
+    for key in ("phi1", "phi2", "disp1", "disp2"):
+        for x, y in zip(a[key], b[key]):
+            assert rel(x, y.cpu().numpy()) <= 1e-6, key

@@ -53,7 +53,7 @@ SMOOTH_BYTES_PER_CELL = 16.0
 # DRAM bytes (read + write) per updated cell of k_smooth_half<6,double> from one ncu
 # capture of the 128^3 launch; scaled per launch by
 # the updated cells.  Set to None whenever the kernel changes.
-SMOOTH_TRAFFIC_PER_UPDATE = None
+SMOOTH_TRAFFIC_PER_UPDATE = 35.8
 
 
 def workload():

@@ -42,6 +42,10 @@ MIXED_INNER_CYCLES = 4
 # GPU arm reports them; the oracle arm scales its one-cycle sample by this.
 CYCLES_PER_STEP = 14
 FP64_PEAK_GOPS = 625.0   # nominal 1.25 TFLOP/s FP64 = 625 G FP64 instructions/s
+HBM_PEAK_GBS = 6765.0    # measured copy bandwidth of the GB300s
+# the roofline describes the dominant launches: half-sweeps of the 128^3 levels
+# (1,048,576 updated cells each); smaller levels are reported beside them
+DOMINANT_UPDATES = 1 << 20
 L2_FLUSH_BYTES = 256 << 20
 
 # smoother: FP64 instructions per updated cell (three 6-neighbour sums: 15 adds,
@@ -412,7 +416,7 @@ def run_ours(args):
     for w in range(args.warmup):
         _, info1, info2 = h.pipeline(deltas, out)
     h.stats(reset=True)
-    h.set_profiling(["smooth"])
+    h.set_profiling(["smooth"], min_cells=DOMINANT_UPDATES)
     sampler = ClockSampler(device.index)
     sampler.start()
     time.sleep(0.4)
@@ -430,18 +434,26 @@ def run_ours(args):
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     stats = h.stats(reset=True)
-    h.set_profiling([])
     value, ms_per_step = aggregate(sum(step_ms), geom.level_cells() * args.steps, args.steps,
                                    dist, device)
     launches = sum(v["launches"] for v in stats.values())
     sm = stats["smooth"]
-    updates_per_launch = sm["cells"] / max(sm["launches"], 1)
+    # dominant launches (the 128^3 levels), timed in the first cycle of each solve
+    updates_per_launch = sm["timed_cells"] / max(sm["timed"], 1)
     ms_per_launch = sm["event_ms"] / max(sm["timed"], 1)
     ops = SMOOTH_OPS_PER_UPDATE[geom.order] * updates_per_launch
     achieved_gops = ops / (ms_per_launch * 1e-3) / 1e9
     smooth_gbs = SMOOTH_BYTES_PER_CELL * 2 * updates_per_launch / (ms_per_launch * 1e-3) / 1e9
-    # event times cover a sample of the launches (the first cycle of each solve)
-    total_smooth_ms = ms_per_launch * sm["launches"]
+    # every level: one more step with every smoother launch of its first cycles timed
+    h.set_profiling(["smooth"], min_cells=0)
+    h.pipeline(deltas, out)
+    sa = h.stats(reset=True)["smooth"]
+    h.set_profiling([])
+    all_ms = sa["event_ms"] / max(sa["timed"], 1)
+    all_updates = sa["timed_cells"] / max(sa["timed"], 1)
+    all_gops = SMOOTH_OPS_PER_UPDATE[geom.order] * all_updates / (all_ms * 1e-3) / 1e9
+    # the sampled launches stand for all smoother launches of the step
+    total_smooth_ms = all_ms * sm["launches"]
 
     # mixed precision on the same workload and stopping rule (float32 V-cycles
     # inside float64 iterative refinement), device-resident like the headline
@@ -468,6 +480,19 @@ def run_ours(args):
         mstats = hm.stats(reset=True)
         mixed_value, mixed_ms_step = aggregate(sum(mixed_ms), geom.level_cells() * args.steps,
                                                args.steps, dist, device)
+        # roofline of the float32 smoother from 3 more steps with CUDA events around
+        # its 128^3 launches (event nodes cost ~1 us each against ~10 us launches,
+        # so the value above is taken without them)
+        hm.set_profiling(["smooth"], min_cells=DOMINANT_UPDATES)
+        for i in range(3):
+            hm.pipeline(deltas, out)
+        msm = hm.stats(reset=True)["smooth"]
+        hm.set_profiling([])
+        m_ms = msm["event_ms"] / max(msm["timed"], 1)
+        m_upd = msm["timed_cells"] / max(msm["timed"], 1)
+        # float32 in place: 8 B per level-cell (read u of both colours 4 B, f of the
+        # updated colour 2 B, write the updated colour 2 B)
+        m_gbs = 8.0 * 2 * m_upd / (m_ms * 1e-3) / 1e9
         mixed = {"value": mixed_value, "unit": UNIT, "ms_per_step": mixed_ms_step,
                  "latency_ms": {"p50": statistics.median(mixed_ms),
                                 "p99": sorted(mixed_ms)[max(0, int(round(0.99 * len(mixed_ms))) - 1)]},
@@ -477,6 +502,12 @@ def run_ours(args):
                  "outer": {"1lpt": m1["cycles"], "2lpt": m2["cycles"]},
                  "rel_residual": {"1lpt": m1["rel_residual"], "2lpt": m2["rel_residual"]},
                  "gpu_launches": sum(v["launches"] for v in mstats.values()),
+                 "roofline": {"bound": "hbm", "achieved": m_gbs, "peak": HBM_PEAK_GBS,
+                              "unit": "GB/s", "frac": m_gbs / HBM_PEAK_GBS, "traffic": None,
+                              "kernel": "k_smooth_half<6,float> (128^3 levels)",
+                              "peak_source": "measured copy bandwidth (of measured)",
+                              "ms_per_launch": m_ms, "updates_per_launch": m_upd,
+                              "bytes_per_cell": 8.0},
                  "error_bound": "<= 1e-6 RMS relative vs float64 (tests/test_gpu_parity.py)"}
         hm.close()
 
@@ -534,12 +565,14 @@ def run_ours(args):
                          "traffic": (SMOOTH_TRAFFIC_PER_UPDATE * updates_per_launch
                                      if SMOOTH_TRAFFIC_PER_UPDATE else None),
                          "traffic_unit": "bytes per launch (ncu, scaled by updated cells)",
-                         "kernel": "k_smooth_half<6,double>",
+                         "kernel": "k_smooth_half<6,double> (128^3 levels)",
                          "peak_source": "nominal FP64 1.25 TFLOP/s (recipe) = 625 G FMA/s",
                          "ms_per_launch": ms_per_launch, "updates_per_launch": updates_per_launch,
-                         "hbm_view": {"achieved_gbs": smooth_gbs, "peak_gbs": 6765.0,
-                                      "frac": smooth_gbs / 6765.0,
+                         "hbm_view": {"achieved_gbs": smooth_gbs, "peak_gbs": HBM_PEAK_GBS,
+                                      "frac": smooth_gbs / HBM_PEAK_GBS,
                                       "bytes_per_cell": SMOOTH_BYTES_PER_CELL},
+                         "all_levels": {"ms_per_launch": all_ms, "updates_per_launch": all_updates,
+                                        "achieved": all_gops, "frac": all_gops / FP64_PEAK_GOPS},
                          "share_of_step": total_smooth_ms / max(sum(step_ms), 1e-9)},
             "gpu_launches": launches,
             "clocks": clocks,

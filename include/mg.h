@@ -56,7 +56,7 @@ typedef enum {
   MG_ENOMEM = 2,   /* the allocator returned NULL                              */
   MG_ENOCONV = 3,  /* max_cycles reached above tol; outputs hold the last iterate */
   MG_ECUDA = 4,    /* a CUDA runtime call or kernel launch failed              */
-  MG_ETIMEOUT = 5  /* reserved: bounded device-side wait expired               */
+  MG_ETIMEOUT = 5  /* a bounded device-side wait ran out; outputs are invalid    */
 } mg_status;
 
 /* MG_FP64: every step in float64.  MG_MIXED: iterative refinement; the
@@ -69,6 +69,13 @@ typedef enum { MG_FP64 = 0, MG_MIXED = 1 } mg_precision;
 /* MG_FLAG_NO_GRAPHS: launch every kernel on the stream instead of replaying one
  * captured CUDA graph per V-cycle (MG_FP64) or per outer iteration (MG_MIXED). */
 #define MG_FLAG_NO_GRAPHS 1
+/* Smoother kernel: by default float32 nests of at least 2^23 cells are smoothed
+ * by the kernel that stages plane tiles in shared memory with the tensor-memory
+ * accelerator, other levels by the kernel that loads every stencil value from
+ * global memory; both give bit-identical results.  MG_FLAG_NO_TMA: the second
+ * kernel on every level.  MG_FLAG_TMA_ALL: the first kernel on every level. */
+#define MG_FLAG_NO_TMA 2
+#define MG_FLAG_TMA_ALL 4
 
 typedef struct {
   int n_levels;                        /* 1 = base only; 1 + number of nests            */
@@ -217,6 +224,7 @@ typedef struct {
   long long cells[MG_K_FAMILIES];     /* cells each family processed (smooth: updated)    */
   double event_ms[MG_K_FAMILIES];     /* summed CUDA-event time of timed launches         */
   long long timed[MG_K_FAMILIES];     /* launches that carried events                     */
+  long long timed_cells[MG_K_FAMILIES]; /* cells of the launches that carried events      */
 } mg_stats;
 
 /* Time launches of the families in mask (bit f = family f) with CUDA event
@@ -226,12 +234,28 @@ typedef struct {
  * mg_stats.timed counts the timed launches. */
 mg_status mg_set_profiling(mg_hierarchy* h, unsigned mask);
 
+/* Restrict the event timing of mg_set_profiling to launches that process at least
+ * min_cells cells (default 0: every launch), e.g. the largest level's launches of
+ * a family.  mg_stats.timed_cells sums the cells of the timed launches. */
+mg_status mg_set_profiling_min_cells(mg_hierarchy* h, long long min_cells);
+
 /* Copy the counters out (synchronising the stream to read event times) and,
  * if reset != 0, zero them. */
 mg_status mg_get_stats(mg_hierarchy* h, mg_stats* out, int reset);
 
 /* Message for the last failing call on h ("" if none; NULL-safe). */
 const char* mg_last_error(const mg_hierarchy* h);
+
+/* Self-test of the device-side wait limit, the failure-detection path of the
+ * TMA-staged smoother (no counterpart in the paper).  Runs that kernel once on an
+ * internal periodic 16^3 float32 level (order 6) with the byte count expected for
+ * its first staged plane raised by 16, so that plane's mbarrier never completes
+ * although every copy lands: the block's bounded wait gives up after about 2 s,
+ * drains its copies, sets the error flag and returns.  Returns MG_ETIMEOUT when
+ * the limit and the error path work, MG_OK if the limit did not trigger (a defect),
+ * MG_ENOMEM or MG_ECUDA on a CUDA failure.  Synchronous; allocates and frees its own
+ * device memory on the current device; the CUDA context stays usable. */
+mg_status mg_selftest_wait_limit(void);
 
 /* Library version string. */
 const char* mg_version(void);

@@ -8,6 +8,7 @@
 // float64 (and 16-byte access for groups of 4 at z = 0 mod 4 for float32).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -72,6 +73,25 @@ cudaError_t launch_prolong(const Grid& F, T* u, const Grid& P, const T* pu, cons
 template <typename T>
 cudaError_t launch_restrict_u(const Grid& F, const T* u, const Grid& P, T* pu, Int3 off,
                               Int3 cn, cudaStream_t s);
+
+// ---- TMA-staged smoother (mg_smooth_tma.cu) ----
+// Same update and result as launch_smooth_half; the input buffer u is read through
+// tin, the source f through tf (both made by make_plane_tmap, with halo = true for
+// u and false for f).  *err is or-ed with 1 when a block's wait for a staged plane
+// ran out.  extra_tx > 0 (wait-limit self-test only) raises the byte count expected
+// for the first staged plane so that its wait runs out.
+template <typename T>
+cudaError_t launch_smooth_half_tma(int order, const Grid& G, const CUtensorMap* tin,
+                                   const CUtensorMap* tf, T* uout, double a_f, int colour,
+                                   int periodic, unsigned* err, cudaStream_t s,
+                                   unsigned extra_tx = 0);
+// Tensor map of one padded level buffer (elem_bytes 4 or 8) for the plane boxes of
+// the TMA smoother: with halo, 72 x (8 + order) elements of z x y; without, 64 x 8.
+cudaError_t make_plane_tmap(const Grid& G, const void* base, int elem_bytes, int order,
+                            bool halo, CUtensorMap* tm);
+bool smooth_tma_usable(const Grid& G);
+// Opt the TMA smoother kernels in to their shared-memory size on the current device.
+cudaError_t prepare_smooth_tma();
 
 // ---- kernels: ghost zones (mg_ghost.cu) ----
 template <typename T>

@@ -57,10 +57,7 @@ __global__ void __launch_bounds__(kPairX * 8)
       out.y = v;
     }
     *reinterpret_cast<V2*>(uout + p0) = out;
-    if (periodic) {
-      write_images<T>(G, uout, i, j, k0, out.x);
-      write_images<T>(G, uout, i, j, k0 + 1, out.y);
-    }
+    if (periodic) write_pair_images<T>(G, uout, i, j, k0, out.x, out.y);
   } else {
     uout[p0] = v;
     if (periodic) write_images<T>(G, uout, i, j, k0, v);
@@ -137,8 +134,8 @@ __global__ void __launch_bounds__(128)
   v.y += d;
   *reinterpret_cast<V2*>(u + p) = v;
   if (periodic) {
-    write_images<T>(F, u, i, j, k0, v.x);
-    write_images<T>(F, u, i, j, k0 + 1, v.y);
+    if (k0 + 1 < F.n2) write_pair_images<T>(F, u, i, j, k0, v.x, v.y);
+    else write_images<T>(F, u, i, j, k0, v.x);
   }
 }
 

@@ -56,31 +56,15 @@ __device__ __forceinline__ T lap_h2(const T* __restrict__ u, long long p, long l
 }
 
 // On a periodic level, every ghost cell is the image of one interior cell (all
-// sides are >= g).  Writes v to the images of interior cell (i, j, k); the cell
-// itself is written by the caller.
-template <typename T>
-__device__ __forceinline__ void write_images(const Grid& G, T* __restrict__ u, int i, int j,
-                                             int k, T v) {
-  const int g = G.g;
-  if (i >= g && i < G.n0 - g && j >= g && j < G.n1 - g && k >= g && k < G.n2 - g) return;
-  int is[2], js[2], ks[2];
-  int ni = 0, nj = 0, nk = 0;
-  if (i < g) is[ni++] = i + G.n0;
-  if (i >= G.n0 - g) is[ni++] = i - G.n0;
-  if (j < g) js[nj++] = j + G.n1;
-  if (j >= G.n1 - g) js[nj++] = j - G.n1;
-  if (k < g) ks[nk++] = k + G.n2;
-  if (k >= G.n2 - g) ks[nk++] = k - G.n2;
-  // all combinations of (own or image) per axis, except own on every axis
-  for (int a = 0; a <= ni; ++a)
-    for (int b = 0; b <= nj; ++b)
-      for (int c = 0; c <= nk; ++c) {
-        if (a == 0 && b == 0 && c == 0) continue;
-        const int ii = a == 0 ? i : is[a - 1];
-        const int jj = b == 0 ? j : js[b - 1];
-        const int kk = c == 0 ? k : ks[c - 1];
-        u[gidx(G, ii, jj, kk)] = v;
-      }
+// sides are >= g).  Along an axis of n cells with element stride st, index a has
+// an image at a + n when a < g and at a - n when a >= n - g (both when n < 2g);
+// ImgAxis holds the element offsets of those images, 0 for none.
+struct ImgAxis {
+  long long lo, hi;
+};
+
+__device__ __forceinline__ ImgAxis img_axis(int a, int n, int g, long long st) {
+  return ImgAxis{a < g ? (long long)n * st : 0, a >= n - g ? -(long long)n * st : 0};
 }
 
 template <typename T>
@@ -93,5 +77,61 @@ template <>
 struct Vec2<float> {
   typedef float2 type;
 };
+
+// Writes v to the images of interior cell (i, j, k): every combination of own
+// or image index per axis except own on every axis.  Straight-line predicated
+// stores (the loops unroll; no local memory); the cell itself is written by the
+// caller.
+template <typename T>
+__device__ __forceinline__ void write_images(const Grid& G, T* __restrict__ u, int i, int j,
+                                             int k, T v) {
+  const int g = G.g;
+  if (i >= g && i < G.n0 - g && j >= g && j < G.n1 - g && k >= g && k < G.n2 - g) return;
+  const long long sy = G.Zp, sx = (long long)G.Y * G.Zp;
+  const ImgAxis ax = img_axis(i, G.n0, g, sx), ay = img_axis(j, G.n1, g, sy),
+                az = img_axis(k, G.n2, g, 1);
+  T* p = u + gidx(G, i, j, k);
+  const long long ox[3] = {0, ax.lo, ax.hi}, oy[3] = {0, ay.lo, ay.hi}, oz[3] = {0, az.lo, az.hi};
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        if ((a | b | c) && (a == 0 || ox[a]) && (b == 0 || oy[b]) && (c == 0 || oz[c]))
+          p[ox[a] + oy[b] + oz[c]] = v;
+}
+
+// Images of the z-pair (k, k+1), k even and k + 1 < n2, with values (va, vb): the
+// x/y images of the pair as one vector store each (x and y offsets are multiples
+// of the row pitch, so the alignment of the pair is kept), the z images of each
+// cell scalar, at the cell's own row and at every x/y image row.
+template <typename T>
+__device__ __forceinline__ void write_pair_images(const Grid& G, T* __restrict__ u, int i, int j,
+                                                  int k, T va, T vb) {
+  const int g = G.g;
+  if (i >= g && i < G.n0 - g && j >= g && j < G.n1 - g && k >= g && k + 1 < G.n2 - g) return;
+  typedef typename Vec2<T>::type V2;
+  const long long sy = G.Zp, sx = (long long)G.Y * G.Zp;
+  const ImgAxis ax = img_axis(i, G.n0, g, sx), ay = img_axis(j, G.n1, g, sy);
+  const ImgAxis z0 = img_axis(k, G.n2, g, 1), z1 = img_axis(k + 1, G.n2, g, 1);
+  T* p = u + gidx(G, i, j, k);
+  const long long ox[3] = {0, ax.lo, ax.hi}, oy[3] = {0, ay.lo, ay.hi};
+  V2 pv;
+  pv.x = va;
+  pv.y = vb;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      if ((a != 0 && !ox[a]) || (b != 0 && !oy[b])) continue;
+      T* q = p + ox[a] + oy[b];
+      if (a | b) *reinterpret_cast<V2*>(q) = pv;
+      if (z0.lo) q[z0.lo] = va;
+      if (z0.hi) q[z0.hi] = va;
+      if (z1.lo) q[1 + z1.lo] = vb;
+      if (z1.hi) q[1 + z1.hi] = vb;
+    }
+}
 
 }  // namespace mgk

@@ -14,6 +14,9 @@ MG_MAX_HISTORY = 64
 MG_FP64 = 0
 MG_MIXED = 1
 MG_FLAG_NO_GRAPHS = 1
+MG_FLAG_NO_TMA = 2
+MG_FLAG_TMA_ALL = 4
+_TMA_FLAGS = {"auto": 0, "off": MG_FLAG_NO_TMA, "all": MG_FLAG_TMA_ALL}
 
 STATUS = {0: "MG_OK", 1: "MG_EINVAL", 2: "MG_ENOMEM", 3: "MG_ENOCONV", 4: "MG_ECUDA",
           5: "MG_ETIMEOUT"}
@@ -69,11 +72,13 @@ class MGStats(ctypes.Structure):
         ("cells", ctypes.c_longlong * MG_K_FAMILIES),
         ("event_ms", ctypes.c_double * MG_K_FAMILIES),
         ("timed", ctypes.c_longlong * MG_K_FAMILIES),
+        ("timed_cells", ctypes.c_longlong * MG_K_FAMILIES),
     ]
 
     def as_dict(self):
         return {name: {"launches": self.launches[i], "cells": self.cells[i],
-                       "event_ms": self.event_ms[i], "timed": self.timed[i]}
+                       "event_ms": self.event_ms[i], "timed": self.timed[i],
+                       "timed_cells": self.timed_cells[i]}
                 for i, name in enumerate(FAMILY_NAMES)}
 
 
@@ -113,6 +118,7 @@ def load_library(path=None):
                                            ctypes.POINTER(MGInfo), ctypes.POINTER(MGInfo)]),
         "mg_set_stream": (ctypes.c_int, [vp, vp]),
         "mg_set_profiling": (ctypes.c_int, [vp, ctypes.c_uint]),
+        "mg_set_profiling_min_cells": (ctypes.c_int, [vp, ctypes.c_longlong]),
         "mg_get_stats": (ctypes.c_int, [vp, ctypes.POINTER(MGStats), ctypes.c_int]),
         "mg_batch_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, vp, ctypes.POINTER(vp)]),
         "mg_batch_destroy": (ctypes.c_int, [vp]),
@@ -121,6 +127,7 @@ def load_library(path=None):
                                                  ctypes.POINTER(MGInfo), ctypes.POINTER(MGInfo)]),
         "mg_batch_last_error": (ctypes.c_char_p, [vp]),
         "mg_last_error": (ctypes.c_char_p, [vp]),
+        "mg_selftest_wait_limit": (ctypes.c_int, []),
         "mg_version": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -133,8 +140,10 @@ def load_library(path=None):
 
 
 def make_config(base_n, box, order, nests=(), precision=MG_FP64, nu1=2, nu2=2, max_cycles=50,
-                tol=1e-10, inner_cycles=2, graphs=True, tile_rows=4):
-    """MGConfig from plain values; nests = [(n3, off3), ...] (off in parent cells)."""
+                tol=1e-10, inner_cycles=2, graphs=True, tile_rows=4, tma="auto"):
+    """MGConfig from plain values; nests = [(n3, off3), ...] (off in parent cells).
+    tma: smoother kernel choice, "auto" (TMA-staged tiles on float32 nests of
+    >= 2^23 cells), "off" or "all"; every choice gives bit-identical results."""
     lib = load_library()
     cfg = MGConfig()
     lib.mg_config_default(ctypes.byref(cfg))
@@ -150,7 +159,7 @@ def make_config(base_n, box, order, nests=(), precision=MG_FP64, nu1=2, nu2=2, m
     cfg.precision = int(precision)
     cfg.nu1, cfg.nu2, cfg.max_cycles, cfg.tol = int(nu1), int(nu2), int(max_cycles), float(tol)
     cfg.inner_cycles = int(inner_cycles)
-    cfg.flags = 0 if graphs else MG_FLAG_NO_GRAPHS
+    cfg.flags = (0 if graphs else MG_FLAG_NO_GRAPHS) | _TMA_FLAGS[tma]
     cfg.tile_rows = int(tile_rows)
     return cfg
 
@@ -287,11 +296,14 @@ class Hierarchy:
         self._check(self.lib.mg_set_stream(self.h, ctypes.c_void_p(stream.cuda_stream)), "mg_set_stream")
         self.stream = stream
 
-    def set_profiling(self, families=()):
-        """Time every launch of the named kernel families with CUDA events."""
+    def set_profiling(self, families=(), min_cells=0):
+        """Time the launches of the named kernel families that process at least
+        min_cells cells with CUDA events."""
         mask = 0
         for name in families:
             mask |= 1 << FAMILY_NAMES.index(name)
+        self._check(self.lib.mg_set_profiling_min_cells(self.h, ctypes.c_longlong(int(min_cells))),
+                    "mg_set_profiling_min_cells")
         self._check(self.lib.mg_set_profiling(self.h, mask), "mg_set_profiling")
 
     def stats(self, reset=False):
@@ -372,3 +384,9 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def selftest_wait_limit():
+    """Runs the device wait-limit self-test (about 2 s); returns the status name,
+    "MG_ETIMEOUT" when the bounded wait and its error path work."""
+    return STATUS.get(int(load_library().mg_selftest_wait_limit()), "unknown")

@@ -46,7 +46,7 @@ class Request:
 def config_key(cfg):
     nests = tuple((tuple(cfg.nest_n[i]), tuple(cfg.nest_off[i])) for i in range(cfg.n_levels - 1))
     return (tuple(cfg.base_n), cfg.box, nests, cfg.order, cfg.precision, cfg.nu1, cfg.nu2,
-            cfg.max_cycles, cfg.inner_cycles, cfg.tile_rows, cfg.tol)
+            cfg.max_cycles, cfg.inner_cycles, cfg.tile_rows, cfg.flags, cfg.tol)
 
 
 class Admission:

@@ -38,14 +38,12 @@ BATCH_SEED = 1000
 SERVE_SEED = 5
 # float32 V-cycles per float64 refinement step in the mixed-precision variant
 MIXED_INNER_CYCLES = 4
-# V-cycles of one full step at SOLVE_TOL on this workload (1LPT + 2LPT), as the
-# GPU arm reports them; the oracle arm scales its one-cycle sample by this.
-CYCLES_PER_STEP = 14
+# V-cycles of one full step (1LPT + 2LPT; unigrid64: 1LPT) at each workload's
+# stopping rule, as the GPU arm reports them; the oracle arm scales its one-cycle
+# sample by this.
+CYCLES_PER_STEP = {"zoom2": 14, "unigrid64": 10, "deep_zoom": 14}
 FP64_PEAK_GOPS = 625.0   # nominal 1.25 TFLOP/s FP64 = 625 G FP64 instructions/s
 HBM_PEAK_GBS = 6765.0    # measured copy bandwidth of the GB300s
-# the roofline describes the dominant launches: half-sweeps of the 128^3 levels
-# (1,048,576 updated cells each); smaller levels are reported beside them
-DOMINANT_UPDATES = 1 << 20
 L2_FLUSH_BYTES = 256 << 20
 
 # smoother: FP64 instructions per updated cell (three 6-neighbour sums: 15 adds,
@@ -60,16 +58,38 @@ SMOOTH_BYTES_PER_CELL = 16.0
 SMOOTH_TRAFFIC_PER_UPDATE = 35.8
 
 
-def workload():
-    from synthetic import config_zoom2
-    return config_zoom2()
+# Workloads: zoom2 is the headline; the others are the single-level and deep-zoom
+# configurations, measured with --workload.  Seeds and stopping rules per workload.
+WORKLOADS = ("zoom2", "unigrid64", "deep_zoom")
+WORKLOAD_SEED = {"zoom2": SEED, "unigrid64": 1, "deep_zoom": 3}
+WORKLOAD_TOL = {"zoom2": SOLVE_TOL, "unigrid64": 1e-10, "deep_zoom": SOLVE_TOL}
+WORKLOAD_TEXT = {
+    "zoom2": "zoom2: 128^3 periodic base (100 Mpc/h) + centred 128^3 nest at 2x, order-6 FD, "
+             "FP64, 1LPT+2LPT+displacements, BBKS z=50, seed 2",
+    "unigrid64": "unigrid64: 64^3 periodic, 7-point Laplacian, FP64, 1LPT (phi and -grad phi) "
+                 "to 1e-10 relative residual, power law P ~ k^-2 at unit RMS, seed 1",
+    "deep_zoom": "deep zoom: 128^3 periodic base (100 Mpc/h) + 4 nests of 128^3, centred with "
+                 "+-16 jitter (seed 3), order-6 FD, FP64, 1LPT+2LPT+displacements, BBKS z=50",
+}
 
 
-def workload_config(geom):
-    return {"workload": "zoom2: 128^3 periodic base (100 Mpc/h) + centred 128^3 nest at 2x, "
-                        "order-6 FD, FP64, 1LPT+2LPT+displacements, BBKS z=50, seed %d" % SEED,
+def workload(name="zoom2"):
+    from synthetic import config_deep_zoom, config_unigrid64, config_zoom2
+    return {"zoom2": config_zoom2, "unigrid64": config_unigrid64,
+            "deep_zoom": config_deep_zoom}[name]()
+
+
+def workload_inputs(name, geom):
+    from synthetic import make_delta, make_delta_powerlaw
+    if name == "unigrid64":
+        return [make_delta_powerlaw(tuple(geom.base_n), WORKLOAD_SEED[name])]
+    return make_delta(geom, WORKLOAD_SEED[name])
+
+
+def workload_config(geom, name="zoom2"):
+    return {"workload": WORKLOAD_TEXT[name],
             "level_cells": geom.level_cells(), "order": geom.order, "levels": geom.n_levels,
-            "solve_tol": SOLVE_TOL, "precision": "fp64",
+            "solve_tol": WORKLOAD_TOL[name], "precision": "fp64",
             "l2": "256 MiB flush written between timed steps, outside the per-step events"}
 
 
@@ -155,10 +175,10 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def cpu_baseline(geom, deltas, cycles_per_step):
+def cpu_baseline(geom, deltas, cycles_per_step, lpt2=True):
     """The oracle on the host cores: one V-cycle, tau and one gradient of the
     same hierarchy, scaled to a full step (cycles_per_step cycles, tau, two
-    gradients)."""
+    gradients; without the 2LPT part: the cycles and one gradient)."""
     from oracle.hierarchy import Hierarchy
     from oracle.lpt import gradient, lpt2_source
     from oracle.multigrid import solve
@@ -171,11 +191,16 @@ def cpu_baseline(geom, deltas, cycles_per_step):
     t0 = time.perf_counter()
     gradient(Hierarchy(geom), phis)
     t_grad = time.perf_counter() - t0
-    t_step = cycles_per_step * t_cycle + t_tau + 2 * t_grad
+    if lpt2:
+        t_step = cycles_per_step * t_cycle + t_tau + 2 * t_grad
+        rest = "tau + 2 gradients"
+    else:
+        t_step = cycles_per_step * t_cycle + t_grad
+        rest = "1 gradient"
     return {"value": geom.level_cells() / t_step, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "1 V-cycle (%.1f s) + tau (%.1f s) + 1 gradient (%.1f s) of the same "
-                      "hierarchy on one host core (numpy), scaled to %d cycles + tau + 2 "
-                      "gradients" % (t_cycle, t_tau, t_grad, cycles_per_step)}
+                      "hierarchy on one host core (numpy), scaled to %d cycles + %s"
+                      % (t_cycle, t_tau, t_grad, cycles_per_step, rest)}
 
 
 def run_reference(args):
@@ -187,15 +212,18 @@ def run_reference(args):
     from oracle.lpt import gradient, lpt2_source
     from oracle.multigrid import solve
     from synthetic import make_delta
-    geom = workload()
-    deltas = make_delta(geom, SEED)
+    name = args.workload
+    geom = workload(name)
+    deltas = workload_inputs(name, geom)
+    lpt2 = name != "unigrid64"
     extra = 0.0
     for w in range(args.warmup):
         phis, _ = solve(geom, deltas, tol=0.0, cycles=1)
         if w == 0:
             t0 = time.perf_counter()
-            lpt2_source(Hierarchy(geom), phis)
-            gradient(Hierarchy(geom), phis)
+            if lpt2:
+                lpt2_source(Hierarchy(geom), phis)
+                gradient(Hierarchy(geom), phis)
             gradient(Hierarchy(geom), phis)
             extra = time.perf_counter() - t0
     times = []
@@ -204,17 +232,19 @@ def run_reference(args):
         solve(geom, deltas, tol=0.0, cycles=1)
         times.append(time.perf_counter() - t0)
     t_cycle = statistics.mean(times)
-    t_step = CYCLES_PER_STEP * t_cycle + extra
+    cycles = CYCLES_PER_STEP[name]
+    t_step = cycles * t_cycle + extra
     value = geom.level_cells() / t_step
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(geom), "impl": "reference",
+            "data": "synthetic", "config": workload_config(geom, name), "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "each step: 1 V-cycle of the FP64 numpy oracle (mean %.2f s); "
-                                       "reported per full step = %d cycles + tau + 2 gradients "
+                                       "reported per full step = %d cycles + %s "
                                        "(%.1f s, timed once in warm-up)"
-                                       % (t_cycle, CYCLES_PER_STEP, extra)},
+                                       % (t_cycle, cycles,
+                                          "tau + 2 gradients" if lpt2 else "1 gradient", extra)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -373,7 +403,8 @@ def batched_measure(pkg, geoms, deltas_np, steps, device):
 def run_ours(args):
     world, rank, local = dist_env()
     batch = None
-    if not args.profile_run and not args.no_batch:
+    name = args.workload
+    if not args.profile_run and not args.no_batch and name == "zoom2":
         batch = batch_inputs(args.serve_large_side if args.serve_seconds > 0 else None)
     import torch
     dist = None
@@ -388,15 +419,20 @@ def run_ours(args):
     import __graft_entry__
     __graft_entry__.build()
     import paper_1103_6031_gb300 as pkg
-    from synthetic import make_delta
 
-    geom = workload()
-    deltas_np = make_delta(geom, SEED)
+    geom = workload(name)
+    deltas_np = workload_inputs(name, geom)
+    tol = WORKLOAD_TOL[name]
+    lpt2 = name != "unigrid64"
+    # the dominant smoother launches: half-sweeps of the largest level
+    from synthetic.geometry import level_shapes
+    dominant = max(n[0] * n[1] * n[2] for n in level_shapes(geom)) // 2
+    big = "%d^3" % round((2 * dominant) ** (1.0 / 3.0))
     if args.profile_run and args.precision == "mixed":
-        cfg = pkg.config_from_geometry(geom, tol=SOLVE_TOL, max_cycles=50, precision=pkg.MG_MIXED,
+        cfg = pkg.config_from_geometry(geom, tol=tol, max_cycles=50, precision=pkg.MG_MIXED,
                                        inner_cycles=MIXED_INNER_CYCLES)
     else:
-        cfg = pkg.config_from_geometry(geom, tol=SOLVE_TOL, max_cycles=50)
+        cfg = pkg.config_from_geometry(geom, tol=tol, max_cycles=50)
     h = pkg.Hierarchy(cfg)
     stream = h.stream
     deltas = [torch.from_numpy(x).to(device) for x in deltas_np]
@@ -412,11 +448,20 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    def step(hh):
+        """One whole step on hierarchy hh; returns the infos of its solves."""
+        if lpt2:
+            _, i1, i2 = hh.pipeline(deltas, out)
+            return i1, i2
+        phis, i1 = hh.solve_1lpt(deltas)
+        hh.displacements(phis)
+        return i1, None
+
     info1 = info2 = None
     for w in range(args.warmup):
-        _, info1, info2 = h.pipeline(deltas, out)
+        info1, info2 = step(h)
     h.stats(reset=True)
-    h.set_profiling(["smooth"], min_cells=DOMINANT_UPDATES)
+    h.set_profiling(["smooth"], min_cells=dominant)
     sampler = ClockSampler(device.index)
     sampler.start()
     time.sleep(0.4)
@@ -427,7 +472,7 @@ def run_ours(args):
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        _, info1, info2 = h.pipeline(deltas, out)
+        info1, info2 = step(h)
         b.record(stream)
         evs.append((a, b))
     barrier()
@@ -438,7 +483,7 @@ def run_ours(args):
                                    dist, device)
     launches = sum(v["launches"] for v in stats.values())
     sm = stats["smooth"]
-    # dominant launches (the 128^3 levels), timed in the first cycle of each solve
+    # dominant launches (the largest level), timed in the first cycle of each solve
     updates_per_launch = sm["timed_cells"] / max(sm["timed"], 1)
     ms_per_launch = sm["event_ms"] / max(sm["timed"], 1)
     ops = SMOOTH_OPS_PER_UPDATE[geom.order] * updates_per_launch
@@ -446,7 +491,7 @@ def run_ours(args):
     smooth_gbs = SMOOTH_BYTES_PER_CELL * 2 * updates_per_launch / (ms_per_launch * 1e-3) / 1e9
     # every level: one more step with every smoother launch of its first cycles timed
     h.set_profiling(["smooth"], min_cells=0)
-    h.pipeline(deltas, out)
+    step(h)
     sa = h.stats(reset=True)["smooth"]
     h.set_profiling([])
     all_ms = sa["event_ms"] / max(sa["timed"], 1)
@@ -459,11 +504,11 @@ def run_ours(args):
     # inside float64 iterative refinement), device-resident like the headline
     mixed = None
     if not args.profile_run:
-        cfg_m = pkg.config_from_geometry(geom, tol=SOLVE_TOL, max_cycles=50,
+        cfg_m = pkg.config_from_geometry(geom, tol=tol, max_cycles=50,
                                          precision=pkg.MG_MIXED, inner_cycles=MIXED_INNER_CYCLES)
         hm = pkg.Hierarchy(cfg_m)
         for w in range(args.warmup):
-            _, m1, m2 = hm.pipeline(deltas, out)
+            m1, m2 = step(hm)
         hm.stats(reset=True)
         barrier()
         evm = []
@@ -472,7 +517,7 @@ def run_ours(args):
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            _, m1, m2 = hm.pipeline(deltas, out)
+            m1, m2 = step(hm)
             b.record(stream)
             evm.append((a, b))
         barrier()
@@ -483,9 +528,9 @@ def run_ours(args):
         # roofline of the float32 smoother from 3 more steps with CUDA events around
         # its 128^3 launches (event nodes cost ~1 us each against ~10 us launches,
         # so the value above is taken without them)
-        hm.set_profiling(["smooth"], min_cells=DOMINANT_UPDATES)
+        hm.set_profiling(["smooth"], min_cells=dominant)
         for i in range(3):
-            hm.pipeline(deltas, out)
+            step(hm)
         msm = hm.stats(reset=True)["smooth"]
         hm.set_profiling([])
         m_ms = msm["event_ms"] / max(msm["timed"], 1)
@@ -499,12 +544,13 @@ def run_ours(args):
                  "precision": "float32 V-cycles (smoothing, transfers, coarse-fine ghosts) inside "
                               "float64 refinement (residual, coarsest solve, update)",
                  "inner_cycles": MIXED_INNER_CYCLES,
-                 "outer": {"1lpt": m1["cycles"], "2lpt": m2["cycles"]},
-                 "rel_residual": {"1lpt": m1["rel_residual"], "2lpt": m2["rel_residual"]},
+                 "outer": {"1lpt": m1["cycles"], "2lpt": m2["cycles"] if m2 else None},
+                 "rel_residual": {"1lpt": m1["rel_residual"],
+                                  "2lpt": m2["rel_residual"] if m2 else None},
                  "gpu_launches": sum(v["launches"] for v in mstats.values()),
                  "roofline": {"bound": "hbm", "achieved": m_gbs, "peak": HBM_PEAK_GBS,
                               "unit": "GB/s", "frac": m_gbs / HBM_PEAK_GBS, "traffic": None,
-                              "kernel": "k_smooth_half<6,float> (128^3 levels)",
+                              "kernel": "k_smooth_half<%d,float> (%s levels)" % (geom.order, big),
                               "peak_source": "measured copy bandwidth (of measured)",
                               "ms_per_launch": m_ms, "updates_per_launch": m_upd,
                               "bytes_per_cell": 8.0},
@@ -522,7 +568,8 @@ def run_ours(args):
     if args.profile_run:
         if rank == 0:
             print(json.dumps({"profile_run": True, "value": value, "ms_per_step": ms_per_step,
-                              "gpu_launches": launches, "cycles": [info1["cycles"], info2["cycles"]]}))
+                              "gpu_launches": launches,
+                              "cycles": [info1["cycles"], info2["cycles"] if info2 else 0]}))
         h.close()
         if dist is not None:
             dist.destroy_process_group()
@@ -534,14 +581,34 @@ def run_ours(args):
                 "phi2": [torch.empty(s, dtype=torch.float64, pin_memory=True) for s in shapes],
                 "disp1": [torch.empty(s, dtype=torch.float64, pin_memory=True) for s in shapes for _ in range(3)],
                 "disp2": [torch.empty(s, dtype=torch.float64, pin_memory=True) for s in shapes for _ in range(3)]}
-    h.pipeline(host_in, host_out, host=True)
+    if not lpt2:
+        # 1LPT only: phi and -grad phi come back (the C ABI's host-buffer entry point
+        # is the whole 2LPT step, so the copies are issued here)
+        host_out = {"phi1": host_out["phi1"], "disp1": host_out["disp1"]}
+
+    def e2e_step():
+        if lpt2:
+            h.pipeline(host_in, host_out, host=True)
+            return
+        with torch.cuda.stream(stream):
+            for d, x in zip(deltas, host_in):
+                d.copy_(x, non_blocking=True)
+            phis, _ = h.solve_1lpt(deltas)
+            disp = h.displacements(phis)
+            for x, y in zip(host_out["phi1"], phis):
+                x.copy_(y, non_blocking=True)
+            for x, y in zip(host_out["disp1"], [c for lv in disp for c in lv]):
+                x.copy_(y, non_blocking=True)
+        stream.synchronize()
+
+    e2e_step()
     barrier()
     e2e_ms = []
     for i in range(args.steps):
         flush.fill_(i & 0xFF)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        h.pipeline(host_in, host_out, host=True)
+        e2e_step()
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     barrier()
@@ -554,18 +621,18 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(geom),
+            "config": workload_config(geom, name),
             "latency_ms": {"p50": statistics.median(step_ms),
                            "p99": sorted(step_ms)[max(0, int(round(0.99 * len(step_ms))) - 1)]},
-            "cycles": {"1lpt": info1["cycles"], "2lpt": info2["cycles"],
+            "cycles": {"1lpt": info1["cycles"], "2lpt": info2["cycles"] if info2 else None,
                        "rel_residual_1lpt": info1["rel_residual"],
-                       "rel_residual_2lpt": info2["rel_residual"]},
+                       "rel_residual_2lpt": info2["rel_residual"] if info2 else None},
             "roofline": {"bound": "alu", "achieved": achieved_gops, "peak": FP64_PEAK_GOPS,
                          "unit": "G FP64 instr/s", "frac": achieved_gops / FP64_PEAK_GOPS,
                          "traffic": (SMOOTH_TRAFFIC_PER_UPDATE * updates_per_launch
-                                     if SMOOTH_TRAFFIC_PER_UPDATE else None),
+                                     if SMOOTH_TRAFFIC_PER_UPDATE and geom.order == 6 else None),
                          "traffic_unit": "bytes per launch (ncu, scaled by updated cells)",
-                         "kernel": "k_smooth_half<6,double> (128^3 levels)",
+                         "kernel": "k_smooth_half<%d,double> (%s levels)" % (geom.order, big),
                          "peak_source": "nominal FP64 1.25 TFLOP/s (recipe) = 625 G FMA/s",
                          "ms_per_launch": ms_per_launch, "updates_per_launch": updates_per_launch,
                          "hbm_view": {"achieved_gbs": smooth_gbs, "peak_gbs": HBM_PEAK_GBS,
@@ -584,7 +651,8 @@ def run_ours(args):
                     "ms_per_step": statistics.mean(e2e_ms)},
         }
         if not args.skip_baseline and world == 1:
-            line["cpu_baseline"] = cpu_baseline(geom, deltas_np, info1["cycles"] + info2["cycles"])
+            line["cpu_baseline"] = cpu_baseline(
+                geom, deltas_np, info1["cycles"] + (info2["cycles"] if info2 else 0), lpt2)
         print(json.dumps(line))
     h.close()
     if dist is not None:
@@ -598,6 +666,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=WORKLOADS, default="zoom2",
+                    help="zoom2 (default, the headline), unigrid64 or deep_zoom")
     ap.add_argument("--skip-baseline", action="store_true",
                     help="leave out the CPU-oracle baseline")
     ap.add_argument("--profile-run", action="store_true",

@@ -300,19 +300,28 @@ def serving_measure(pkg, geoms, deltas_np, large, seconds, rate, workers):
     for k in range(n):
         if rng.uniform() < 0.1:
             reqs.append(serve.Request(k, cfg_large, large_in))
+            reqs[-1].cls = "large"
             cells += large[0].level_cells()
         else:
             i = int(rng.integers(len(geoms)))
             reqs.append(serve.Request(k, cfg_small[i], pinned[i]))
+            reqs[-1].cls = "batch_draw"
             cells += geoms[i].level_cells()
     server = serve.Server(workers=workers, hbm_budget=64 << 30, keep_outputs=False)
     wall = serve.run_open_loop(server, reqs, rate, seed=SERVE_SEED)
     errors = [r for r in reqs if r.error is not None]
     stats = serve.latency_stats(reqs)
+    by_class = {}
+    for c in ("batch_draw", "large"):
+        sub = [r for r in reqs if r.cls == c]
+        if sub:
+            st = serve.latency_stats(sub)
+            by_class[c] = {"count": st["count"], "p50": st["p50_ms"], "p99": st["p99_ms"]}
     out = {"offered_rate_per_s": rate, "requests": n, "seconds_of_arrivals": seconds,
            "completed_per_s": n / wall, "level_cells_per_s": cells / wall,
            "latency_ms": {"p50": stats["p50_ms"], "p99": stats["p99_ms"], "mean": stats["mean_ms"],
                           "max": stats["max_ms"]},
+           "latency_ms_by_class": by_class,
            "workers": workers, "peak_inflight": server.peak_inflight,
            "peak_resident_gb": server.admission.peak / 2 ** 30,
            "evictions": server.admission.evictions, "errors": len(errors),

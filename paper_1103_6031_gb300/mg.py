@@ -212,6 +212,9 @@ class Hierarchy:
         import torch
         self._torch = torch
         self.lib = load_library()
+        # a private copy: the allocator fields set below belong to this hierarchy, and
+        # the caller's struct may be shared by threads creating hierarchies at once
+        cfg = MGConfig.from_buffer_copy(cfg)
         self.cfg = cfg
         self.shapes = [tuple(cfg.base_n)] + [tuple(cfg.nest_n[i]) for i in range(cfg.n_levels - 1)]
         self.device = torch.device("cuda", torch.cuda.current_device())

@@ -10,7 +10,8 @@ as a worker slot is free and their hierarchy fits the HBM budget:
   budget, evicting idle cached hierarchies (least recently used) when needed;
 * device-resident level state: hierarchies are cached by configuration, so a
   request whose geometry was seen before reuses the resident levels and its
-  captured CUDA graphs;
+  captured CUDA graphs; when requests of one configuration overlap, the cache
+  holds several instances of it (budget permitting) so they run concurrently;
 * overlap: every worker drives its own CUDA stream and the library call holds
   no Python lock, so requests that arrive while others are on the GPU run
   concurrently with them;
@@ -52,9 +53,11 @@ def config_key(cfg):
 class Admission:
     """HBM-budget bookkeeping of resident hierarchies, keyed by configuration.
 
-    entries: key -> [handle, bytes, busy].  reserve() hands out an idle cached
-    entry, or makes room for a new one by closing idle entries (least recently
-    used first); it returns None when the request cannot run now."""
+    cache: key -> list of entries [handle, bytes, busy] (one per resident
+    instance of that configuration).  reserve() hands out an idle cached
+    instance, or makes room for a new one by closing idle instances (least
+    recently used configuration first); it returns None when the request cannot
+    run now."""
 
     def __init__(self, budget, workspace_bytes=None, close=None):
         self.budget = int(budget)
@@ -65,37 +68,50 @@ class Admission:
         self.peak = 0
         self.evictions = 0
 
+    def _idle_lru(self):
+        for key, entries in self.cache.items():
+            for e in entries:
+                if not e[2]:
+                    return key, e
+        return None
+
     def reserve(self, key, cfg):
-        entry = self.cache.get(key)
-        if entry is not None:
-            if entry[2]:
-                return None
-            entry[2] = True
-            self.cache.move_to_end(key)
-            return entry
+        for e in self.cache.get(key, ()):
+            if not e[2]:
+                e[2] = True
+                self.cache.move_to_end(key)
+                return e
         need = self.workspace_bytes(cfg)
         while self.resident + need > self.budget:
-            victim = next((k for k, e in self.cache.items() if not e[2]), None)
+            victim = self._idle_lru()
             if victim is None:
                 return None
-            handle, nbytes, _ = self.cache.pop(victim)
-            if handle is not None:
-                self.close_handle(handle)
-            self.resident -= nbytes
+            vkey, ventry = victim
+            self.cache[vkey].remove(ventry)
+            if not self.cache[vkey]:
+                del self.cache[vkey]
+            if ventry[0] is not None:
+                self.close_handle(ventry[0])
+            self.resident -= ventry[1]
             self.evictions += 1
         entry = [None, need, True]
-        self.cache[key] = entry
+        self.cache.setdefault(key, []).append(entry)
+        self.cache.move_to_end(key)
         self.resident += need
         self.peak = max(self.peak, self.resident)
         return entry
+
+    def instances(self, key):
+        return len(self.cache.get(key, ()))
 
     def release(self, entry):
         entry[2] = False
 
     def clear(self):
-        for handle, _, _ in self.cache.values():
-            if handle is not None:
-                self.close_handle(handle)
+        for entries in self.cache.values():
+            for handle, _, _ in entries:
+                if handle is not None:
+                    self.close_handle(handle)
         self.cache.clear()
         self.resident = 0
 

@@ -45,6 +45,21 @@ def test_admission_never_evicts_busy_entries():
     assert adm.reserve("B", "b") is not None and adm.resident == 30
 
 
+def test_admission_runs_overlapping_requests_of_one_config_on_separate_instances():
+    adm, closed = _adm(100, {"a": 40})
+    e1 = adm.reserve("A", "a")
+    e2 = adm.reserve("A", "a")                     # first instance busy: a second one
+    assert e1 is not None and e2 is not None and e1 is not e2
+    assert adm.instances("A") == 2 and adm.resident == 80
+    assert adm.reserve("A", "a") is None           # a third would exceed the budget
+    adm.release(e2)
+    assert adm.reserve("A", "a") is e2             # idle instance reused
+    adm.release(e1)
+    adm.release(e2)
+    adm.reserve("A", "a")
+    assert adm.instances("A") == 2 and closed == [] and adm.evictions == 0
+
+
 GEOMS = [
     (small_zoom(16, ((16, 4),), order=2, box=20.0), 0),
     (small_zoom(24, ((20, 7),), order=6, box=50.0), 1),
@@ -92,3 +107,48 @@ def test_results_are_identical_alone_and_in_the_mix():
             for key in ("phi1", "phi2", "disp1", "disp2"):
                 for a, b in zip(r.outputs[key], out[key]):
                     assert torch.equal(a, b), (r.id, key)
+
+
+@pytest.mark.gpu
+def test_concurrent_creation_from_one_shared_config():
+    """Several worker threads create hierarchies from one shared config struct at
+    once (the serving cache holds several instances of a busy configuration); the
+    binding works on private copies, so the caller's struct is never written and
+    every instance solves correctly."""
+    import threading
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1103_6031_gb300 as pkg
+    geom = small_zoom(24, ((20, 7),), order=6, box=50.0)
+    cfg = pkg.config_from_geometry(geom, tol=1e-9, max_cycles=40)
+    deltas = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in make_delta(geom, 91)]
+    ref = pkg.Hierarchy(cfg)
+    want, _, _ = ref.pipeline(deltas, host=True)
+    ref.close()
+    results, errors = [None] * 8, []
+
+    def work(i):
+        try:
+            torch.cuda.set_device(0)
+            s = torch.cuda.Stream()
+            with torch.cuda.stream(s):
+                h = pkg.Hierarchy(cfg, stream=s)
+                results[i], _, _ = h.pipeline(deltas, host=True)
+                h.close()
+        except Exception as exc:  # reported below
+            errors.append(exc)
+
+    threads = [threading.Thread(target=work, args=(i,)) for i in range(8)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    assert not cfg.dev_alloc and not cfg.dev_free
+    for out in results:
+        for key in ("phi1", "phi2", "disp1", "disp2"):
+            for a, b in zip(out[key], want[key]):
+                assert torch.equal(a, b), key

@@ -333,6 +333,51 @@ def serving_measure(pkg, geoms, deltas_np, large, seconds, rate, workers):
     return out
 
 
+def generator_measure(pkg, steps, with_oracle):
+    """Periodic BBKS density fields on the GPU (Philox white noise + cuFFT
+    convolution, mg_field_generate) for 128^3 and 256^3 base grids of a 100 Mpc/h
+    box, CUDA-event timed; the numpy oracle of the same field on one host core
+    beside it (128^3 only)."""
+    import numpy as np
+    import torch
+    from synthetic.spectra import BBKSPower
+    res = {}
+    for side in (128, 256):
+        h = 100.0 / side
+        nt = 8192
+        dk = 2 * np.pi / h * np.sqrt(3) * 0.5 * 1.01 / (nt - 1)
+        k = np.arange(nt) * dk
+        amp = np.sqrt(BBKSPower()(np.maximum(k, 1e-12)) / h ** 3)
+        amp[0] = 0.0
+        f = pkg.Field((side,) * 3, h, amp, dk)
+        out = torch.empty((side,) * 3, dtype=torch.float64, device="cuda")
+        s = torch.cuda.current_stream()
+        for w in range(3):
+            f.generate(w, out)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        for i in range(steps):
+            f.generate(100 + i, out)
+        b.record(s)
+        b.synchronize()
+        ms = a.elapsed_time(b) / steps
+        entry = {"ms_per_field": ms, "cells_per_s": side ** 3 / (ms * 1e-3)}
+        if side == 128 and with_oracle:
+            from oracle.noise import gaussian_field, white_noise
+            t0 = time.perf_counter()
+            gaussian_field(white_noise(7, side ** 3).reshape((side,) * 3), h, amp, dk)
+            t = time.perf_counter() - t0
+            entry["cpu_oracle"] = {"cells_per_s": side ** 3 / t, "cores": 1, "kind": "oracle",
+                                   "sample": "one 128^3 field (numpy: Philox, Box-Muller, FFT)"}
+        res["%d^3" % side] = entry
+        f.close()
+    res["what"] = ("white noise (Philox4x32-10 + Box-Muller) and its periodic convolution with "
+                   "a BBKS amplitude table (cuFFT D2Z, amplitude kernel, Z2D), in place")
+    return res
+
+
 def batched_measure(pkg, geoms, deltas_np, steps, device):
     """Hierarchies/s on the batched workload: the float64 solve one hierarchy at a
     time against the mixed-precision batch (one graph launch per iteration)."""
@@ -566,6 +611,10 @@ def run_ours(args):
                  "error_bound": "<= 1e-6 RMS relative vs float64 (tests/test_gpu_parity.py)"}
         hm.close()
 
+    generator = None
+    if not args.profile_run and name == "zoom2":
+        generator = generator_measure(pkg, args.steps, world == 1 and not args.skip_baseline)
+
     batched = None
     serving = None
     if batch is not None:
@@ -655,6 +704,7 @@ def run_ours(args):
             "mixed_precision": mixed,
             "batched": batched,
             "serving": serving,
+            "generator": generator,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h,
                     "ms_per_step": statistics.mean(e2e_ms)},

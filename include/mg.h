@@ -257,6 +257,44 @@ const char* mg_last_error(const mg_hierarchy* h);
  * device memory on the current device; the CUDA context stays usable. */
 mg_status mg_selftest_wait_limit(void);
 
+/* ---- Density generator (Hahn & Abel 2011, Sec. 2.1) ----------------------------
+ * Gaussian white noise from a counter-based generator and its periodic
+ * convolution with a radial amplitude: delta = IFFT[A(|k|) FFT[noise]], the
+ * k-space form of the paper's delta = T * mu on a periodic level. */
+
+/* out[i], i in [0, n): standard normal deviates.  Element i comes from pair index
+ * q = i / 2: Philox4x32-10 (Salmon et al. 2011) with counter (q mod 2^32,
+ * q div 2^32, 0, 0) and key (seed mod 2^32, seed div 2^32) gives four 32-bit words
+ * x0..x3; u1 = ((x0 >> 5) 2^26 + (x1 >> 6) + 1/2) / 2^53, u2 likewise from x2, x3;
+ * out[2q] = r cos(2 pi u2), out[2q+1] = r sin(2 pi u2), r = sqrt(-2 ln u1).
+ * out: device pointer, 16-byte aligned, n doubles.  Asynchronous on cuda_stream.
+ * Errors: MG_EINVAL (n < 0, NULL or misaligned out), MG_ECUDA (launch). */
+mg_status mg_white_noise(unsigned long long seed, long long n, double* out, void* cuda_stream);
+
+typedef struct mg_field mg_field;  /* opaque: FFT plans and spectrum of one grid size */
+
+/* A generator for periodic n0 x n1 x n2 grids of cubic cells of side h (grid sides
+ * 2..4096).  The amplitude A(|k|) is the linear interpolation of amp[0..nt) (host,
+ * nt >= 2, finite), sampled at |k| = t dk; A = 0 beyond (nt - 1) dk and at k = 0.
+ * For the density of Sec. 2.1 with numpy-style unnormalised transforms, A = sqrt(P(k)
+ * / h^3).  Allocates the half spectrum (16 n0 n1 (n2/2+1) bytes) and two cuFFT plans
+ * on the current device.  Errors: MG_EINVAL, MG_ENOMEM, MG_ECUDA. */
+mg_status mg_field_create(int n0, int n1, int n2, double h, const double* amp, int nt,
+                          double dk, mg_field** out);
+
+/* delta = IFFT[A(|k|) FFT[noise]] / (n0 n1 n2 normalisation of the inverse), both
+ * dense [x][y][z] doubles on the device (they may be the same buffer).  Asynchronous
+ * on cuda_stream; calls on one generator must not overlap (they share its spectrum). */
+mg_status mg_field_convolve(mg_field* g, const double* noise, double* delta, void* cuda_stream);
+
+/* delta = the field of the white noise mg_white_noise(seed, n0 n1 n2) (generated in
+ * delta itself, then convolved in place). */
+mg_status mg_field_generate(mg_field* g, unsigned long long seed, double* delta,
+                            void* cuda_stream);
+
+const char* mg_field_last_error(const mg_field* g);  /* "" if none; NULL-safe */
+mg_status mg_field_destroy(mg_field* g);             /* NULL-safe */
+
 /* Library version string. */
 const char* mg_version(void);
 

@@ -128,6 +128,14 @@ def load_library(path=None):
         "mg_batch_last_error": (ctypes.c_char_p, [vp]),
         "mg_last_error": (ctypes.c_char_p, [vp]),
         "mg_selftest_wait_limit": (ctypes.c_int, []),
+        "mg_white_noise": (ctypes.c_int, [ctypes.c_ulonglong, ctypes.c_longlong, vp, vp]),
+        "mg_field_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                           ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                           ctypes.c_double, ctypes.POINTER(vp)]),
+        "mg_field_convolve": (ctypes.c_int, [vp, vp, vp, vp]),
+        "mg_field_generate": (ctypes.c_int, [vp, ctypes.c_ulonglong, vp, vp]),
+        "mg_field_last_error": (ctypes.c_char_p, [vp]),
+        "mg_field_destroy": (ctypes.c_int, [vp]),
         "mg_version": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -393,3 +401,90 @@ def selftest_wait_limit():
     """Runs the device wait-limit self-test (about 2 s); returns the status name,
     "MG_ETIMEOUT" when the bounded wait and its error path work."""
     return STATUS.get(int(load_library().mg_selftest_wait_limit()), "unknown")
+
+
+def _dense_f64(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda \
+            or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous float64 CUDA tensor" % name)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def white_noise(seed, n, out=None, stream=None):
+    """n standard normal deviates from Philox4x32-10 (see mg_white_noise), on the GPU."""
+    import torch
+    if out is None:
+        out = torch.empty(int(n), dtype=torch.float64, device="cuda")
+    if out.numel() != int(n):
+        raise ValueError("out must hold n elements")
+    stream = stream or torch.cuda.current_stream()
+    st = load_library().mg_white_noise(int(seed), int(n), _dense_f64(out, "out"),
+                                       ctypes.c_void_p(stream.cuda_stream))
+    if st != 0:
+        raise MGError(st, "mg_white_noise")
+    return out
+
+
+class Field:
+    """Periodic Gaussian field generator for one grid size (mg_field_*):
+    delta = IFFT[A(|k|) FFT[noise]] with A linearly interpolated from `amp`
+    sampled at |k| = t dk."""
+
+    def __init__(self, shape, h, amp, dk):
+        import numpy as np
+        self.lib = load_library()
+        self.shape = tuple(int(n) for n in shape)
+        table = np.ascontiguousarray(amp, dtype=np.float64)
+        handle = ctypes.c_void_p()
+        st = self.lib.mg_field_create(self.shape[0], self.shape[1], self.shape[2], float(h),
+                                      table.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                      int(table.size), float(dk), ctypes.byref(handle))
+        if st != 0:
+            raise MGError(st, "mg_field_create")
+        self.g = handle
+
+    def _out(self, out):
+        import torch
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.float64, device="cuda")
+        if tuple(out.shape) != self.shape:
+            raise ValueError("output shape %s != %s" % (tuple(out.shape), self.shape))
+        return out
+
+    def _check(self, st, what):
+        if st != 0:
+            msg = self.lib.mg_field_last_error(self.g)
+            raise MGError(st, "%s: %s" % (what, msg.decode() if msg else ""))
+
+    def convolve(self, noise, out=None, stream=None):
+        import torch
+        out = self._out(out)
+        if tuple(noise.shape) != self.shape:
+            raise ValueError("noise shape %s != %s" % (tuple(noise.shape), self.shape))
+        stream = stream or torch.cuda.current_stream()
+        self._check(self.lib.mg_field_convolve(self.g, _dense_f64(noise, "noise"),
+                                               _dense_f64(out, "out"),
+                                               ctypes.c_void_p(stream.cuda_stream)),
+                    "mg_field_convolve")
+        return out
+
+    def generate(self, seed, out=None, stream=None):
+        import torch
+        out = self._out(out)
+        stream = stream or torch.cuda.current_stream()
+        self._check(self.lib.mg_field_generate(self.g, int(seed), _dense_f64(out, "out"),
+                                               ctypes.c_void_p(stream.cuda_stream)),
+                    "mg_field_generate")
+        return out
+
+    def close(self):
+        if getattr(self, "g", None):
+            self.lib.mg_field_destroy(self.g)
+            self.g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -103,6 +103,6 @@ def test_white_noise_field_has_the_table_spectrum():
     a = amplitude(kmag(shape, h), table, dk)
     a.flat[0] = 0.0
     # E|delta_k|^2 = N A^2 for unit white noise; the ratio averages to 1
-    ratio = np.abs(np.fft.fftn(d)) ** 2 / (np.prod(shape) * np.maximum(a, 1e-300) ** 2)
     sel = a > 0
-    assert abs(ratio[sel].mean() - 1.0) < 0.02
+    ratio = np.abs(np.fft.fftn(d))[sel] ** 2 / (np.prod(shape) * a[sel] ** 2)
+    assert abs(ratio.mean() - 1.0) < 0.02

@@ -14,12 +14,15 @@
   removed).  Positions follow x = q + D1 psi1 + (3/7) D1^2 psi2 with
   psi = -grad phi for both potentials (Scoccimarro 1998 sign convention; the
   paper's eq. for L and its D2 = 3/7 D+^2 differ in sign, see Sec. 3.1).
+* Local Lagrangian density (Sec. 5.3): rho / rho_bar = 1 / det[delta_ij +
+  dL_i/dq_j] from the same finite-difference Hessian, renormalised to unit
+  composite mean.
 """
 
 import numpy as np
 
-from .hierarchy import Hierarchy, fill_ghosts
-from .multigrid import solve, sync_covered
+from .hierarchy import Hierarchy, fill_ghosts, restrict
+from .multigrid import composite_mean, solve, sync_covered
 from .stencils import GRADIENT_1D, LAPLACIAN_1D
 
 
@@ -115,3 +118,32 @@ def lpt_pipeline(geom, deltas, tol=1e-10, max_cycles=50, cycles=None):
     psi2 = gradient(hier, phi2)
     return {"phi1": phi1, "phi2": phi2, "psi1": psi1, "psi2": psi2,
             "info1": info1, "info2": info2}
+
+
+def lla_density(hier, phis1, phis2=None, a1=1.0, a2=0.0):
+    """rho / rho_bar by the local Lagrangian approximation (Sec. 5.3, eq. for the
+    gas density): 1 / det[delta_ij + dL_i/dq_j] with the displacement
+    L = a1 psi1 + a2 psi2 = -grad(a1 phi1 + a2 phi2), so dL_i/dq_j = -Phi_,ij with
+    Phi = a1 phi1 + a2 phi2 and Phi_,ij the finite differences of the 2LPT source.
+    Covered cells hold the mean of their children; then the mass is restored by
+    rho -> rho + (1 - <rho>), <.> the volume-weighted composite leaf mean (the
+    paper's a-posteriori renormalisation, read as an additive shift)."""
+    pot = [a1 * np.asarray(p1) + (a2 * np.asarray(p2) if phis2 is not None else 0.0)
+           for p1, p2 in zip(phis1, phis2 if phis2 is not None else phis1)]
+    load_potential(hier, pot)
+    fields = []
+    for l in hier.leaf_levels():
+        fill_ghosts(hier, l, edges=True)
+        diag, mixed = second_derivatives(hier.levels[l])
+        jac = np.empty(tuple(hier.levels[l].n) + (3, 3))
+        for a in range(3):
+            jac[..., a, a] = 1.0 - diag[a]
+            for b in range(a + 1, 3):
+                jac[..., a, b] = -mixed[(a, b)]
+                jac[..., b, a] = -mixed[(a, b)]
+        fields.append(1.0 / np.linalg.det(jac))
+    leaf = list(hier.leaf_levels())
+    for i in range(len(leaf) - 1, 0, -1):
+        fields[i - 1][hier.covered_region(leaf[i])] = restrict(fields[i])
+    mean = composite_mean(hier, fields)
+    return [f + (1.0 - mean) for f in fields]

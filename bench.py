@@ -41,7 +41,7 @@ MIXED_INNER_CYCLES = 4
 # V-cycles of one full step (1LPT + 2LPT; unigrid64: 1LPT) at each workload's
 # stopping rule, as the GPU arm reports them; the oracle arm scales its one-cycle
 # sample by this.
-CYCLES_PER_STEP = {"zoom2": 14, "unigrid64": 10, "deep_zoom": 14}
+CYCLES_PER_STEP = {"zoom2": 14, "unigrid64": 9, "deep_zoom": 14}
 FP64_PEAK_GOPS = 625.0   # nominal 1.25 TFLOP/s FP64 = 625 G FP64 instructions/s
 HBM_PEAK_GBS = 6765.0    # measured copy bandwidth of the GB300s
 L2_FLUSH_BYTES = 256 << 20

@@ -153,6 +153,20 @@ mg_status mg_displacements(mg_hierarchy* h, const double* const phi[], double* c
  * the average of their children.  Same layout as delta. */
 mg_status mg_lpt2_source(mg_hierarchy* h, const double* const phi1[], double* const tau[]);
 
+/* Local Lagrangian approximation of the density (Sec. 5.3, eq. for rho(q, t)):
+ * rho[l] = rho / rho_bar = 1 / det[delta_ij + dL_i/dq_j] for the displacement
+ * L = a1 psi1 + a2 psi2 = -grad(a1 phi1 + a2 phi2) (e.g. a1 = D1, a2 = 3/7 D1^2), i.e.
+ * dL_i/dq_j = -Phi_,ij with Phi = a1 phi1 + a2 phi2 and the finite-difference
+ * Hessian of the 2LPT source (Phi_,ii: 1D second difference; Phi_,ij: G_i G_j, with
+ * edge ghosts on nests).  Covered cells hold the mean of their children; the field
+ * is then shifted so that its volume-weighted composite leaf mean is exactly 1
+ * (mass conservation).  Where det <= 0 (shell crossing) the approximation does not
+ * hold and the result is 1/det as computed.  phi1, rho: device, dense per leaf level;
+ * phi2 may be NULL (a2 unused).  Overwrites the hierarchy's float64 state and leaf
+ * sources.  Errors: MG_EINVAL (NULL pointers, non-finite a1/a2), MG_ECUDA. */
+mg_status mg_lla_density(mg_hierarchy* h, const double* const phi1[], const double* const phi2[],
+                         double a1, double a2, double* const rho[]);
+
 /* One whole initial-conditions step: phi1 = solve(delta), phi2 = solve(tau(phi1)),
  * disp1 = -G phi1, disp2 = -G phi2.  host_buffers != 0: every pointer is a host
  * pointer and the call copies inputs in and outputs out on its stream (pinned

@@ -871,13 +871,15 @@ mg_status load_leaf(mg_hierarchy* h, int l, const double* src, double* padded, b
   return MG_OK;
 }
 
-mg_status store_leaf(mg_hierarchy* h, int l, const double* padded, double* dst, bool host) {
+// add (device buffers only): dst = interior + add
+mg_status store_leaf(mg_hierarchy* h, int l, const double* padded, double* dst, bool host,
+                     double add = 0.0) {
   DevLevel& L = h->L[l];
   if (host) {
     cudaMemcpy3DParms p = dense_padded_parms(L, const_cast<double*>(padded), dst, false);
     CK(cudaMemcpy3DAsync(&p, h->s));
   } else {
-    KL(MG_K_COPY, cells_of(L.G), launch_unpack(L.G, padded, dst, h->s));
+    KL(MG_K_COPY, cells_of(L.G), launch_unpack(L.G, padded, dst, h->s, add));
   }
   return MG_OK;
 }
@@ -1498,6 +1500,51 @@ mg_status mg_displacements(mg_hierarchy* h, const double* const phi[], double* c
   return on_streams(h, [&]() -> mg_status {
     ST(load_potential(h, phi, false));
     ST(gradient_out(h, disp, false));
+    CK(cudaStreamSynchronize(h->s));
+    return MG_OK;
+  });
+}
+
+mg_status mg_lla_density(mg_hierarchy* h, const double* const phi1[], const double* const phi2[],
+                         double a1, double a2, double* const rho[]) {
+  if (!h) return MG_EINVAL;
+  const int nleaf = n_leaf(h);
+  if (!check_ptrs((const void* const*)phi1, nleaf) || !check_ptrs((const void* const*)rho, nleaf))
+    return fail(h, MG_EINVAL, "phi1/rho must hold one non-NULL pointer per level");
+  if (phi2 && !check_ptrs((const void* const*)phi2, nleaf))
+    return fail(h, MG_EINVAL, "phi2 must be NULL or hold one non-NULL pointer per level");
+  if (!std::isfinite(a1) || !std::isfinite(a2))
+    return fail(h, MG_EINVAL, "a1 and a2 must be finite");
+  return on_streams(h, [&]() -> mg_status {
+    // Phi = a1 phi1 + a2 phi2 into the float64 u of every leaf level
+    for (int l = h->base; l <= finest(h); ++l) {
+      DevLevel& L = h->L[l];
+      const int i = l - h->base;
+      KL(MG_K_COPY, cells_of(L.G),
+         launch_axpby(cells_of(L.G), a1, phi1[i], a2, phi2 ? phi2[i] : nullptr, h->scratch, h->s));
+      ST(load_leaf(h, l, h->scratch, phi_of(L), false));
+      L.d.ghosts_stale = true;
+    }
+    ST(sync_covered(h));
+    for (int l = h->base + 1; l <= finest(h); ++l) ST(tangential<double>(h, l));
+    // 1/det[I - H] - 1 into f, covered cells := mean of children
+    for (int l = h->base; l <= finest(h); ++l) {
+      DevLevel& L = h->L[l];
+      ST(ghost_fill<double>(h, l, true));
+      KL(MG_K_LPT, cells_of(L.G),
+         launch_lla(h->cfg.order, L.G, phi_of(L), 1.0 / (L.geo.h * L.geo.h), L.f, h->tau_work,
+                    h->s));
+    }
+    for (int l = finest(h); l > h->base; --l) {
+      DevLevel& L = h->L[l];
+      DevLevel& P = h->L[l - 1];
+      KL(MG_K_RESTRICT, cells_of(L.G),
+         launch_restrict_u<double>(L.G, L.f, P.G, P.f, L.off, L.cn, h->s));
+    }
+    // unit composite mean: remove the volume-weighted leaf mean, then add 1 on output
+    ST(remove_source_mean(h));
+    for (int l = h->base; l <= finest(h); ++l)
+      ST(store_leaf(h, l, h->L[l].f, rho[l - h->base], false, 1.0));
     CK(cudaStreamSynchronize(h->s));
     return MG_OK;
   });

@@ -133,7 +133,9 @@ cudaError_t launch_reduce_partials(const double* partial, int count, int width, 
                                    cudaStream_t s);
 cudaError_t launch_pack(const Grid& G, const double* src, double* dst, double shift,
                         cudaStream_t s);
-cudaError_t launch_unpack(const Grid& G, const double* src, double* dst, cudaStream_t s);
+// dense dst = padded interior of src + add
+cudaError_t launch_unpack(const Grid& G, const double* src, double* dst, cudaStream_t s,
+                          double add = 0.0);
 cudaError_t launch_shift_copy(const Grid& G, double* f, double* f2, const double* mean_num,
                               double inv_volume, cudaStream_t s);
 cudaError_t launch_fill(double* p, long long n, double v, cudaStream_t s);
@@ -141,6 +143,13 @@ cudaError_t launch_fill(double* p, long long n, double v, cudaStream_t s);
 // float64 for the first derivatives.
 cudaError_t launch_lpt2_source(int order, const Grid& G, const double* phi, double invh2,
                                double* tau, double* work, cudaStream_t s);
+// 1/det[I - H] - 1 on the interior (H: finite-difference Hessian of phi, ghosts and
+// edges filled); work holds 3 * grid_elems(G) float64.
+cudaError_t launch_lla(int order, const Grid& G, const double* phi, double invh2, double* out,
+                       double* work, cudaStream_t s);
+// out = a1 x1 + a2 x2 over n dense elements (x2 may be NULL)
+cudaError_t launch_axpby(long long n, double a1, const double* x1, double a2, const double* x2,
+                         double* out, cudaStream_t s);
 cudaError_t launch_gradient(int order, const Grid& G, const double* phi, double invh, double* dx,
                             double* dy, double* dz, cudaStream_t s);
 

@@ -181,12 +181,12 @@ __global__ void __launch_bounds__(256)
 }
 
 __global__ void __launch_bounds__(256)
-    k_unpack(Grid G, const double* __restrict__ src, double* __restrict__ dst) {
+    k_unpack(Grid G, const double* __restrict__ src, double* __restrict__ dst, double add) {
   const long long n = (long long)G.n0 * G.n1 * G.n2;
   const long long t = blockIdx.x * 256LL + threadIdx.x;
   if (t >= n) return;
   const int k = (int)(t % G.n2), j = (int)((t / G.n2) % G.n1), i = (int)(t / ((long long)G.n2 * G.n1));
-  dst[t] = __ldg(src + gidx(G, i, j, k));
+  dst[t] = __ldg(src + gidx(G, i, j, k)) + add;
 }
 
 // f -= mean, f2 = f on the interior; mean = *mean_num * inv_volume (device-side).
@@ -260,22 +260,17 @@ __global__ void __launch_bounds__(128)
   }
 }
 
-// tau = sum_{i<j} (phi_ii phi_jj - phi_ij^2): phi_ii is the 1D second
-// difference along i, phi_ij = G_i (G_j phi) from the stored first derivatives.
+// Finite-difference Hessian at element p: d[a] = phi_aa, the 1D second difference
+// along a; m = (phi_xy, phi_xz, phi_yz), phi_ab = G_a (G_b phi) from the stored
+// first derivatives.
 template <int ORDER>
-__global__ void __launch_bounds__(128)
-    k_lpt2_source(Grid G, const double* __restrict__ phi, const double* __restrict__ dx,
-                  const double* __restrict__ dy, const double* __restrict__ dz, double invh2,
-                  double* __restrict__ tau) {
+__device__ __forceinline__ void fd_hessian(const Grid& G, const double* __restrict__ phi,
+                                           const double* __restrict__ dy,
+                                           const double* __restrict__ dz, double invh2,
+                                           long long p, double (&d)[3], double (&m)[3]) {
   constexpr int half = ORDER / 2;
-  const int k = blockIdx.x * 32 + threadIdx.x;
-  const int j = blockIdx.y * 4 + threadIdx.y;
-  const int i = blockIdx.z;
-  if (k >= G.n2 || j >= G.n1) return;
-  const long long p = gidx(G, i, j, k);
   const long long st[3] = {(long long)G.Y * G.Zp, (long long)G.Zp, 1};
   const double c = __ldg(phi + p);
-  double d[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     double acc = Lap<ORDER>::w0 * c;
@@ -287,7 +282,6 @@ __global__ void __launch_bounds__(128)
   // phi_xy = G_x D_y, phi_xz = G_x D_z, phi_yz = G_y D_z
   const double* src[3] = {dy, dz, dz};
   const int ax[3] = {0, 0, 1};
-  double m[3];
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
     double acc = 0.0;
@@ -297,7 +291,53 @@ __global__ void __launch_bounds__(128)
                 acc);
     m[q] = acc * invh2;
   }
+}
+
+// tau = sum_{i<j} (phi_ii phi_jj - phi_ij^2) (Sec. 3.1.2).
+template <int ORDER>
+__global__ void __launch_bounds__(128)
+    k_lpt2_source(Grid G, const double* __restrict__ phi, const double* __restrict__ dx,
+                  const double* __restrict__ dy, const double* __restrict__ dz, double invh2,
+                  double* __restrict__ tau) {
+  const int k = blockIdx.x * 32 + threadIdx.x;
+  const int j = blockIdx.y * 4 + threadIdx.y;
+  const int i = blockIdx.z;
+  if (k >= G.n2 || j >= G.n1) return;
+  const long long p = gidx(G, i, j, k);
+  double d[3], m[3];
+  fd_hessian<ORDER>(G, phi, dy, dz, invh2, p, d, m);
   tau[p] = fma(d[0], d[1] + d[2], d[1] * d[2]) - fma(m[0], m[0], fma(m[1], m[1], m[2] * m[2]));
+}
+
+// Local Lagrangian density (Sec. 5.3): with H the Hessian of the combined
+// potential Phi (L = -grad Phi), rho / rho_bar = 1 / det[I - H]; writes
+// 1/det - 1 (the renormalisation and the +1 follow on the host side).
+// det[I - H] = a b c - a m_yz^2 - b m_xz^2 - c m_xy^2 - 2 m_xy m_xz m_yz with
+// a, b, c = 1 - phi_xx, 1 - phi_yy, 1 - phi_zz.
+template <int ORDER>
+__global__ void __launch_bounds__(128)
+    k_lla(Grid G, const double* __restrict__ phi, const double* __restrict__ dy,
+          const double* __restrict__ dz, double invh2, double* __restrict__ out) {
+  const int k = blockIdx.x * 32 + threadIdx.x;
+  const int j = blockIdx.y * 4 + threadIdx.y;
+  const int i = blockIdx.z;
+  if (k >= G.n2 || j >= G.n1) return;
+  const long long p = gidx(G, i, j, k);
+  double d[3], m[3];
+  fd_hessian<ORDER>(G, phi, dy, dz, invh2, p, d, m);
+  const double a = 1.0 - d[0], b = 1.0 - d[1], c = 1.0 - d[2];
+  const double det = a * b * c - a * m[2] * m[2] - b * m[1] * m[1] - c * m[0] * m[0] -
+                     2.0 * m[0] * m[1] * m[2];
+  out[p] = 1.0 / det - 1.0;
+}
+
+// out[t] = a1 x1[t] + a2 x2[t] (x2 may be NULL) over n dense elements.
+__global__ void __launch_bounds__(256)
+    k_axpby(long long n, double a1, const double* __restrict__ x1, double a2,
+            const double* __restrict__ x2, double* __restrict__ out) {
+  const long long t = blockIdx.x * 256LL + threadIdx.x;
+  if (t >= n) return;
+  out[t] = x2 ? fma(a2, __ldg(x2 + t), a1 * __ldg(x1 + t)) : a1 * __ldg(x1 + t);
 }
 
 template <int ORDER>
@@ -381,9 +421,10 @@ cudaError_t launch_pack(const Grid& G, const double* src, double* dst, double sh
   return cudaGetLastError();
 }
 
-cudaError_t launch_unpack(const Grid& G, const double* src, double* dst, cudaStream_t s) {
+cudaError_t launch_unpack(const Grid& G, const double* src, double* dst, cudaStream_t s,
+                          double add) {
   const long long n = (long long)G.n0 * G.n1 * G.n2;
-  k_unpack<<<blocks_for(n, 256), 256, 0, s>>>(G, src, dst);
+  k_unpack<<<blocks_for(n, 256), 256, 0, s>>>(G, src, dst, add);
   return cudaGetLastError();
 }
 
@@ -439,6 +480,40 @@ cudaError_t launch_lpt2_source(int order, const Grid& G, const double* phi, doub
       break;
     default: return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lla(int order, const Grid& G, const double* phi, double invh2, double* out,
+                       double* work, cudaStream_t s) {
+  const long long e = grid_elems(G);
+  double* dx = work;
+  double* dy = work + e;
+  double* dz = work + 2 * e;
+  const dim3 block(32, 4, 1);
+  const dim3 gpad((G.n2 + 2 * G.g + 31) / 32, (G.n1 + 2 * G.g + 3) / 4, G.n0 + 2 * G.g);
+  const dim3 gin((G.n2 + 31) / 32, (G.n1 + 3) / 4, G.n0);
+  switch (order) {
+    case 2:
+      k_first_derivs<2><<<gpad, block, 0, s>>>(G, phi, dx, dy, dz);
+      k_lla<2><<<gin, block, 0, s>>>(G, phi, dy, dz, invh2, out);
+      break;
+    case 4:
+      k_first_derivs<4><<<gpad, block, 0, s>>>(G, phi, dx, dy, dz);
+      k_lla<4><<<gin, block, 0, s>>>(G, phi, dy, dz, invh2, out);
+      break;
+    case 6:
+      k_first_derivs<6><<<gpad, block, 0, s>>>(G, phi, dx, dy, dz);
+      k_lla<6><<<gin, block, 0, s>>>(G, phi, dy, dz, invh2, out);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpby(long long n, double a1, const double* x1, double a2, const double* x2,
+                         double* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_axpby<<<blocks_for(n, 256), 256, 0, s>>>(n, a1, x1, a2, x2, out);
   return cudaGetLastError();
 }
 

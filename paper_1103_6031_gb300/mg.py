@@ -128,6 +128,8 @@ def load_library(path=None):
         "mg_batch_last_error": (ctypes.c_char_p, [vp]),
         "mg_last_error": (ctypes.c_char_p, [vp]),
         "mg_selftest_wait_limit": (ctypes.c_int, []),
+        "mg_lla_density": (ctypes.c_int, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_double,
+                                          ctypes.c_double, ctypes.POINTER(vp)]),
         "mg_white_noise": (ctypes.c_int, [ctypes.c_ulonglong, ctypes.c_longlong, vp, vp]),
         "mg_field_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                            ctypes.POINTER(ctypes.c_double), ctypes.c_int,
@@ -282,6 +284,16 @@ class Hierarchy:
         st = self.lib.mg_displacements(self.h, _ptrs(phi, self.shapes), _ptrs(flat))
         self._check(st, "mg_displacements")
         return disp
+
+    def lla_density(self, phi1, phi2=None, a1=1.0, a2=0.0):
+        """rho / rho_bar per leaf level by the local Lagrangian approximation of the
+        displacement -grad(a1 phi1 + a2 phi2) (mg_lla_density)."""
+        rho = [self._empty(s) for s in self.shapes]
+        st = self.lib.mg_lla_density(self.h, _ptrs(phi1, self.shapes),
+                                     _ptrs(phi2, self.shapes) if phi2 is not None else None,
+                                     float(a1), float(a2), _ptrs(rho))
+        self._check(st, "mg_lla_density")
+        return rho
 
     def pipeline(self, deltas, outputs=None, host=False, allow_noconv=False):
         """Whole step; `outputs` = dict of preallocated lists (phi1, phi2, disp1, disp2)."""

@@ -76,6 +76,10 @@ typedef enum { MG_FP64 = 0, MG_MIXED = 1 } mg_precision;
  * kernel on every level.  MG_FLAG_TMA_ALL: the first kernel on every level. */
 #define MG_FLAG_NO_TMA 2
 #define MG_FLAG_TMA_ALL 4
+/* MG_FLAG_HYBRID: the displacements of mg_lpt_pipeline and mg_batch_lpt_pipeline get
+ * the hybrid Poisson solver correction on the finest level (Sec. 3.5.2, see
+ * mg_hybrid_correction) with that level's source (delta for psi1, tau for psi2). */
+#define MG_FLAG_HYBRID 8
 
 typedef struct {
   int n_levels;                        /* 1 = base only; 1 + number of nests            */
@@ -152,6 +156,19 @@ mg_status mg_displacements(mg_hierarchy* h, const double* const phi[], double* c
 /* The 2LPT source tau on every level (before mean removal); covered cells hold
  * the average of their children.  Same layout as delta. */
 mg_status mg_lpt2_source(mg_hierarchy* h, const double* const phi1[], double* const tau[]);
+
+/* Hybrid Poisson solver correction (Sec. 3.5.2): psi[c] (c = x, y, z; dense device
+ * arrays of the finest level) += IFFT[i (k_c / k^2 + g_c / Lt) FFT[f]], the exact
+ * k-space gradient of the inverse Laplacian minus its order-n finite-difference
+ * counterpart (Table 1 symbols: Lt = -sum_a lam_n(k_a h) / h^2, i g_c = i g_n(k_c h) / h),
+ * applied to the finest level's own source f (dense, device), which is zero outside
+ * the level: a nest is zero-padded to twice its size; a single periodic level is
+ * corrected periodically.  The multiplier is 0 at k = 0 and on the Nyquist plane of
+ * axis c.  psi = -G phi, so psi + correction is the exact k-space displacement of
+ * the level's own source plus the multigrid long-range part.  Allocates (on first use;
+ * kept until mg_hierarchy_destroy) a real and two complex grids of the (padded) level
+ * and cuFFT plans.  Errors: MG_EINVAL, MG_ECUDA. */
+mg_status mg_hybrid_correction(mg_hierarchy* h, const double* f, double* const psi[3]);
 
 /* Local Lagrangian approximation of the density (Sec. 5.3, eq. for rho(q, t)):
  * rho[l] = rho / rho_bar = 1 / det[delta_ij + dL_i/dq_j] for the displacement

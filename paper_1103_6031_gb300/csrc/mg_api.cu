@@ -143,6 +143,9 @@ struct mg_hierarchy {
   double* scratch = nullptr;   // 3 dense arrays of the largest leaf level
   long long scratch_elems = 0;
   double* tau_work = nullptr;  // 3 padded float64 arrays of the largest leaf level
+  // hybrid Poisson correction of the finest level (MG_FLAG_HYBRID), made on first use
+  HybridFFT* hybrid = nullptr;
+  double* hybrid_f = nullptr;  // dense source of the finest level
   double volume = 0.0;
   // launch counters and optional CUDA-event timing per kernel family
   mg_stats stats;
@@ -914,8 +917,21 @@ mg_status tau_into_f(mg_hierarchy* h) {
   return MG_OK;
 }
 
-// -G phi of the potential in the float64 u; outputs dense, 3 per leaf level.
-mg_status gradient_out(mg_hierarchy* h, double* const disp[], bool host) {
+// The finest level's psi (3 dense device arrays) += the hybrid correction of the
+// level's current source f (Sec. 3.5.2); plans and buffers are made on first use.
+mg_status hybrid_into(mg_hierarchy* h, const double* f_dense, double* const psi[3]) {
+  DevLevel& L = h->L[finest(h)];
+  if (!h->hybrid) {
+    CK(hybrid_create(&h->hybrid, L.G.n0, L.G.n1, L.G.n2, L.geo.h, h->cfg.order, !L.periodic));
+  }
+  CK(hybrid_apply(h->hybrid, f_dense, psi, h->s));
+  return MG_OK;
+}
+
+// -G phi of the potential in the float64 u; outputs dense, 3 per leaf level.  With
+// hybrid (and MG_FLAG_HYBRID), the finest level's psi also gets the hybrid
+// correction of the source in f (the source of the potential just solved for).
+mg_status gradient_out(mg_hierarchy* h, double* const disp[], bool host, bool hybrid = false) {
   for (int l = h->base; l <= finest(h); ++l) {
     DevLevel& L = h->L[l];
     const int i = l - h->base;
@@ -924,11 +940,18 @@ mg_status gradient_out(mg_hierarchy* h, double* const disp[], bool host) {
     double* dy = disp[3 * i + 1];
     double* dz = disp[3 * i + 2];
     const long long n = (long long)L.G.n0 * L.G.n1 * L.G.n2;
+    const bool hyb = hybrid && l == finest(h) && (h->cfg.flags & MG_FLAG_HYBRID);
+    if (hyb && !h->hybrid_f) CK(cudaMalloc(&h->hybrid_f, n * sizeof(double)));
+    if (hyb) ST(store_leaf(h, l, L.f, h->hybrid_f, false));
     if (host) {
       if (!dx && !dy && !dz) continue;
       KL(MG_K_LPT, n,
          launch_gradient(h->cfg.order, L.G, phi_of(L), 1.0 / L.geo.h, h->scratch,
                          h->scratch + n, h->scratch + 2 * n, h->s));
+      if (hyb) {
+        double* const psi[3] = {h->scratch, h->scratch + n, h->scratch + 2 * n};
+        ST(hybrid_into(h, h->hybrid_f, psi));
+      }
       for (int a = 0; a < 3; ++a)
         if (disp[3 * i + a])
           CK(cudaMemcpyAsync(disp[3 * i + a], h->scratch + a * n, n * sizeof(double),
@@ -936,6 +959,10 @@ mg_status gradient_out(mg_hierarchy* h, double* const disp[], bool host) {
     } else {
       if (!dx || !dy || !dz) return fail(h, MG_EINVAL, "displacement output pointer is NULL");
       KL(MG_K_LPT, n, launch_gradient(h->cfg.order, L.G, phi_of(L), 1.0 / L.geo.h, dx, dy, dz, h->s));
+      if (hyb) {
+        double* const psi[3] = {dx, dy, dz};
+        ST(hybrid_into(h, h->hybrid_f, psi));
+      }
     }
   }
   return MG_OK;
@@ -1132,7 +1159,7 @@ mg_status batch_pipeline(mg_batch* b, bool host, const double* const* const delt
     if (phi1 && phi1[i])
       for (int l = h->base; l <= finest(h) && r == MG_OK; ++l)
         if (phi1[i][l - h->base]) r = store_leaf(h, l, phi_of(h->L[l]), phi1[i][l - h->base], host);
-    if (r == MG_OK && disp1 && disp1[i]) r = gradient_out(h, disp1[i], host);
+    if (r == MG_OK && disp1 && disp1[i]) r = gradient_out(h, disp1[i], host, true);
     if (r == MG_OK) r = tau_into_f(h);
     if (r != MG_OK) return member_status(b, (int)i, r);
   }
@@ -1144,7 +1171,7 @@ mg_status batch_pipeline(mg_batch* b, bool host, const double* const* const delt
     if (phi2 && phi2[i])
       for (int l = h->base; l <= finest(h) && r == MG_OK; ++l)
         if (phi2[i][l - h->base]) r = store_leaf(h, l, phi_of(h->L[l]), phi2[i][l - h->base], host);
-    if (r == MG_OK && disp2 && disp2[i]) r = gradient_out(h, disp2[i], host);
+    if (r == MG_OK && disp2 && disp2[i]) r = gradient_out(h, disp2[i], host, true);
     if (r != MG_OK) return member_status(b, (int)i, r);
   }
   for (size_t i = 0; i < n; ++i) BCK(cudaStreamSynchronize(b->m[i]->s));
@@ -1253,7 +1280,13 @@ mg_status mg_config_validate(const mg_config* cfg, char* msg, size_t len) {
 size_t mg_workspace_bytes(const mg_config* cfg) {
   Plan p;
   if (!validate(cfg, nullptr, 0, &p)) return 0;
-  return p.bytes;
+  size_t extra = 0;
+  if (cfg->flags & MG_FLAG_HYBRID) {
+    const LevelGeom& f = p.geo.back();
+    extra = hybrid_bytes(f.n[0], f.n[1], f.n[2], f.nest) +
+            (size_t)f.n[0] * f.n[1] * f.n[2] * sizeof(double);
+  }
+  return p.bytes + extra;
 }
 
 int mg_total_levels(const mg_config* cfg) {
@@ -1432,6 +1465,8 @@ mg_status mg_hierarchy_destroy(mg_hierarchy* h) {
     else cudaFree(h->arena);
   }
   if (h->host_red) cudaFreeHost(h->host_red);
+  hybrid_destroy(h->hybrid);
+  cudaFree(h->hybrid_f);
   for (int f = 0; f < MG_K_FAMILIES; ++f) {
     for (cudaEvent_t e : h->ev_start[f]) cudaEventDestroy(e);
     for (cudaEvent_t e : h->ev_end[f]) cudaEventDestroy(e);
@@ -1505,6 +1540,17 @@ mg_status mg_displacements(mg_hierarchy* h, const double* const phi[], double* c
   });
 }
 
+mg_status mg_hybrid_correction(mg_hierarchy* h, const double* f, double* const psi[3]) {
+  if (!h) return MG_EINVAL;
+  if (!f || !psi || !psi[0] || !psi[1] || !psi[2])
+    return fail(h, MG_EINVAL, "f and the three psi components must be non-NULL");
+  return on_streams(h, [&]() -> mg_status {
+    ST(hybrid_into(h, f, psi));
+    CK(cudaStreamSynchronize(h->s));
+    return MG_OK;
+  });
+}
+
 mg_status mg_lla_density(mg_hierarchy* h, const double* const phi1[], const double* const phi2[],
                          double a1, double a2, double* const rho[]) {
   if (!h) return MG_EINVAL;
@@ -1570,14 +1616,14 @@ mg_status mg_lpt_pipeline(mg_hierarchy* h, int host_buffers, const double* const
     if (phi1)
       for (int l = h->base; l <= finest(h); ++l)
         if (phi1[l - h->base]) ST(store_leaf(h, l, phi_of(h->L[l]), phi1[l - h->base], host));
-    if (disp1) ST(gradient_out(h, disp1, host));
+    if (disp1) ST(gradient_out(h, disp1, host, true));
     ST(tau_into_f(h));
     mg_status st2 = solve_prepared(h, info2);
     if (st2 != MG_OK && st2 != MG_ENOCONV) return st2;
     if (phi2)
       for (int l = h->base; l <= finest(h); ++l)
         if (phi2[l - h->base]) ST(store_leaf(h, l, phi_of(h->L[l]), phi2[l - h->base], host));
-    if (disp2) ST(gradient_out(h, disp2, host));
+    if (disp2) ST(gradient_out(h, disp2, host, true));
     CK(cudaStreamSynchronize(h->s));
     return st1 != MG_OK ? st1 : st2;
   });

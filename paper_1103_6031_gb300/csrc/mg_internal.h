@@ -155,4 +155,15 @@ cudaError_t launch_gradient(int order, const Grid& G, const double* phi, double 
 
 int norm_blocks(const Grid& G);
 
+// ---- hybrid Poisson solver correction (mg_hybrid.cu) ----
+struct HybridFFT;
+// Plans and buffers for an n0 x n1 x n2 level of spacing h (pad: zero-padded to 2x).
+cudaError_t hybrid_create(HybridFFT** out, int n0, int n1, int n2, double h, int order,
+                          bool pad);
+void hybrid_destroy(HybridFFT* hy);
+// psi[c] (dense, device) += the correction of source f (dense, device), c = 0, 1, 2.
+cudaError_t hybrid_apply(HybridFFT* hy, const double* f, double* const psi[3], cudaStream_t s);
+// device bytes of hybrid_create for that level (buffers and an estimate of cuFFT's work area)
+size_t hybrid_bytes(int n0, int n1, int n2, bool pad);
+
 }  // namespace mgk

@@ -16,6 +16,7 @@ MG_MIXED = 1
 MG_FLAG_NO_GRAPHS = 1
 MG_FLAG_NO_TMA = 2
 MG_FLAG_TMA_ALL = 4
+MG_FLAG_HYBRID = 8
 _TMA_FLAGS = {"auto": 0, "off": MG_FLAG_NO_TMA, "all": MG_FLAG_TMA_ALL}
 
 STATUS = {0: "MG_OK", 1: "MG_EINVAL", 2: "MG_ENOMEM", 3: "MG_ENOCONV", 4: "MG_ECUDA",
@@ -128,6 +129,7 @@ def load_library(path=None):
         "mg_batch_last_error": (ctypes.c_char_p, [vp]),
         "mg_last_error": (ctypes.c_char_p, [vp]),
         "mg_selftest_wait_limit": (ctypes.c_int, []),
+        "mg_hybrid_correction": (ctypes.c_int, [vp, vp, ctypes.POINTER(vp)]),
         "mg_lla_density": (ctypes.c_int, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_double,
                                           ctypes.c_double, ctypes.POINTER(vp)]),
         "mg_white_noise": (ctypes.c_int, [ctypes.c_ulonglong, ctypes.c_longlong, vp, vp]),
@@ -150,10 +152,12 @@ def load_library(path=None):
 
 
 def make_config(base_n, box, order, nests=(), precision=MG_FP64, nu1=2, nu2=2, max_cycles=50,
-                tol=1e-10, inner_cycles=2, graphs=True, tile_rows=4, tma="auto"):
+                tol=1e-10, inner_cycles=2, graphs=True, tile_rows=4, tma="auto", hybrid=False):
     """MGConfig from plain values; nests = [(n3, off3), ...] (off in parent cells).
     tma: smoother kernel choice, "auto" (TMA-staged tiles on float32 nests of
-    >= 2^23 cells), "off" or "all"; every choice gives bit-identical results."""
+    >= 2^23 cells), "off" or "all"; every choice gives bit-identical results.
+    hybrid: the pipelines add the hybrid Poisson correction (Sec. 3.5.2) to the
+    finest level's displacements."""
     lib = load_library()
     cfg = MGConfig()
     lib.mg_config_default(ctypes.byref(cfg))
@@ -169,7 +173,8 @@ def make_config(base_n, box, order, nests=(), precision=MG_FP64, nu1=2, nu2=2, m
     cfg.precision = int(precision)
     cfg.nu1, cfg.nu2, cfg.max_cycles, cfg.tol = int(nu1), int(nu2), int(max_cycles), float(tol)
     cfg.inner_cycles = int(inner_cycles)
-    cfg.flags = (0 if graphs else MG_FLAG_NO_GRAPHS) | _TMA_FLAGS[tma]
+    cfg.flags = (0 if graphs else MG_FLAG_NO_GRAPHS) | _TMA_FLAGS[tma] | \
+        (MG_FLAG_HYBRID if hybrid else 0)
     cfg.tile_rows = int(tile_rows)
     return cfg
 
@@ -284,6 +289,15 @@ class Hierarchy:
         st = self.lib.mg_displacements(self.h, _ptrs(phi, self.shapes), _ptrs(flat))
         self._check(st, "mg_displacements")
         return disp
+
+    def hybrid_correction(self, f, psi):
+        """psi (3 dense tensors of the finest level) += the hybrid Poisson correction
+        of the finest level's source f (mg_hybrid_correction); returns psi."""
+        shape = self.shapes[-1]
+        fp = _ptrs([f], [shape])
+        st = self.lib.mg_hybrid_correction(self.h, ctypes.c_void_p(fp[0]), _ptrs(list(psi), [shape] * 3))
+        self._check(st, "mg_hybrid_correction")
+        return psi
 
     def lla_density(self, phi1, phi2=None, a1=1.0, a2=0.0):
         """rho / rho_bar per leaf level by the local Lagrangian approximation of the

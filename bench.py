@@ -548,6 +548,14 @@ def run_ours(args):
     step(h)
     sa = h.stats(reset=True)["smooth"]
     h.set_profiling([])
+
+    # open-loop serving, measured early in the process: after the batched and
+    # autotuning sections (hundreds of hierarchies made and destroyed) its latency
+    # was measured up to 10x worse than in a fresh process
+    serving = None
+    if batch is not None and args.serve_seconds > 0 and world == 1:
+        serving = serving_measure(pkg, batch[0], batch[1], batch[2], args.serve_seconds,
+                                  args.serve_rate, args.serve_workers)
     all_ms = sa["event_ms"] / max(sa["timed"], 1)
     all_updates = sa["timed_cells"] / max(sa["timed"], 1)
     all_gops = SMOOTH_OPS_PER_UPDATE[geom.order] * all_updates / (all_ms * 1e-3) / 1e9
@@ -616,12 +624,8 @@ def run_ours(args):
         generator = generator_measure(pkg, args.steps, world == 1 and not args.skip_baseline)
 
     batched = None
-    serving = None
     if batch is not None:
         batched = batched_measure(pkg, batch[0], batch[1], min(args.steps, 3), device)
-        if args.serve_seconds > 0 and world == 1:
-            serving = serving_measure(pkg, batch[0], batch[1], batch[2], args.serve_seconds,
-                                      args.serve_rate, args.serve_workers)
 
     if args.profile_run:
         if rank == 0:

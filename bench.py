@@ -549,9 +549,9 @@ def run_ours(args):
     sa = h.stats(reset=True)["smooth"]
     h.set_profiling([])
 
-    # open-loop serving, measured early in the process: after the batched and
-    # autotuning sections (hundreds of hierarchies made and destroyed) its latency
-    # was measured up to 10x worse than in a fresh process
+    # open-loop serving, measured early in the process: measured after the batched
+    # and autotuning sections (hundreds of hierarchies made and destroyed), its p50
+    # latency was 15x worse than in a fresh process
     serving = None
     if batch is not None and args.serve_seconds > 0 and world == 1:
         serving = serving_measure(pkg, batch[0], batch[1], batch[2], args.serve_seconds,

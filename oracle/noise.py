@@ -18,7 +18,7 @@ counter-based generator from its published definition:
   last place so that 0 and 1 never occur).
 
 Element i of the noise comes from pair index q = i // 2: counter (q mod 2^32,
-q div 2^32, 0, 0), key (seed mod 2^32, seed div 2^32); outputs x0..x3 give
+q div 2^32, stream, 0), key (seed mod 2^32, seed div 2^32); outputs x0..x3 give
 u1 = ((x0 >> 5) 2^26 + (x1 >> 6) + 1/2) / 2^53 and u2 likewise from x2, x3;
 element 2q = r cos(2 pi u2), element 2q + 1 = r sin(2 pi u2), r = sqrt(-2 ln u1).
 
@@ -65,13 +65,14 @@ def uniform53(a, b):
     return (hi * 67108864.0 + lo + 0.5) / 9007199254740992.0
 
 
-def white_noise(seed, n):
-    """n standard normal deviates, element i from pair index i // 2 (see header)."""
+def white_noise(seed, n, stream=0):
+    """n standard normal deviates, element i from pair index i // 2 (see header);
+    stream goes into counter word 2 (0 for a single field; the level of a nest)."""
     seed = int(seed)
     pairs = (int(n) + 1) // 2
     q = np.arange(pairs, dtype=np.uint64)
     ctr = np.stack([(q & _LO).astype(np.uint32), (q >> np.uint64(32)).astype(np.uint32),
-                    np.zeros(pairs, np.uint32), np.zeros(pairs, np.uint32)])
+                    np.full(pairs, int(stream) & 0xFFFFFFFF, np.uint32), np.zeros(pairs, np.uint32)])
     key = (np.uint32(seed & 0xFFFFFFFF), np.uint32((seed >> 32) & 0xFFFFFFFF))
     x = philox4x32_10(ctr, key)
     u1 = uniform53(x[0], x[1])

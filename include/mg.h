@@ -324,6 +324,26 @@ mg_status mg_field_generate(mg_field* g, unsigned long long seed, double* delta,
                             void* cuda_stream);
 
 const char* mg_field_last_error(const mg_field* g);  /* "" if none; NULL-safe */
+
+/* Multi-scale density on the nested hierarchy cfg describes (Sec. 2.3), into
+ * delta[l] (device, dense per leaf level, base first):
+ *  - noise: level l draws mg_white_noise's deviates with counter word 2 = l;
+ *  - nests: Hoffman-Ribak constraint (Sec. 2.3.1), the mean of the 8 children of
+ *    each parent cell := parent noise / sqrt(8);
+ *  - base: periodic field IFFT[A FFT[noise]], A(|k|) = sqrt_p(|k|) / h^{3/2} with
+ *    sqrt_p[0..nt) (host) sampled at |k| = t dk as for mg_field_create;
+ *  - nest: isolated field of its own noise (zero-padded to twice its size) plus
+ *    the parent-level field of all noise outside it (its parent's noise with the
+ *    nest region zeroed, convolved like the parent's own, plus what the parent
+ *    carried), brought down by conservative tricubic interpolation (tensor cubic
+ *    Lagrange through 4 parent cells, then each group of 8 children shifted to
+ *    average to the parent value) (Sec. 2.3.3-2.3.4);
+ *  - covered cells hold the mean of their 8 children.
+ * Allocates its work arrays and cuFFT plans on the current device for the call;
+ * synchronous on cuda_stream.  Errors: MG_EINVAL (invalid cfg or table), MG_ENOMEM,
+ * MG_ECUDA. */
+mg_status mg_density_multiscale(const mg_config* cfg, unsigned long long seed, const double* sqrt_p,
+                                int nt, double dk, double* const delta[], void* cuda_stream);
 mg_status mg_field_destroy(mg_field* g);             /* NULL-safe */
 
 /* Library version string. */

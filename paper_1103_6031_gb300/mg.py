@@ -140,6 +140,9 @@ def load_library(path=None):
         "mg_field_generate": (ctypes.c_int, [vp, ctypes.c_ulonglong, vp, vp]),
         "mg_field_last_error": (ctypes.c_char_p, [vp]),
         "mg_field_destroy": (ctypes.c_int, [vp]),
+        "mg_density_multiscale": (ctypes.c_int, [ctypes.POINTER(MGConfig), ctypes.c_ulonglong,
+                                                 ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                                 ctypes.c_double, ctypes.POINTER(vp), vp]),
         "mg_version": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -514,3 +517,21 @@ class Field:
             self.close()
         except Exception:
             pass
+
+
+def density_multiscale(cfg, seed, sqrt_p, dk, out=None, stream=None):
+    """delta on every leaf level of the hierarchy cfg describes (mg_density_multiscale);
+    sqrt_p: sqrt(P(|k|)) sampled at |k| = t dk.  Returns the list of device tensors."""
+    import numpy as np
+    import torch
+    shapes = [tuple(cfg.base_n)] + [tuple(cfg.nest_n[i]) for i in range(cfg.n_levels - 1)]
+    if out is None:
+        out = [torch.empty(sh, dtype=torch.float64, device="cuda") for sh in shapes]
+    table = np.ascontiguousarray(sqrt_p, dtype=np.float64)
+    stream = stream or torch.cuda.current_stream()
+    st = load_library().mg_density_multiscale(
+        ctypes.byref(cfg), int(seed), table.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+        int(table.size), float(dk), _ptrs(out, shapes), ctypes.c_void_p(stream.cuda_stream))
+    if st != 0:
+        raise MGError(st, "mg_density_multiscale")
+    return out

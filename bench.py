@@ -375,6 +375,27 @@ def generator_measure(pkg, steps, with_oracle):
         f.close()
     res["what"] = ("white noise (Philox4x32-10 + Box-Muller) and its periodic convolution with "
                    "a BBKS amplitude table (cuFFT D2Z, amplitude kernel, Z2D), in place")
+    # the multi-scale field of the zoom2 hierarchy (128^3 base + 128^3 nest): noise per
+    # level, Hoffman-Ribak, periodic and zero-padded convolutions, carried outside field
+    from synthetic import config_zoom2
+    geom = config_zoom2()
+    nt = 8192
+    h = geom.box / geom.base_n[0] / 2
+    dk = 2 * np.pi / h * np.sqrt(3) * 0.5 * 1.01 / (nt - 1)
+    k = np.arange(nt) * dk
+    sqrt_p = np.sqrt(BBKSPower()(np.maximum(k, 1e-12)))
+    sqrt_p[0] = 0.0
+    cfg = pkg.config_from_geometry(geom)
+    from paper_1103_6031_gb300 import mg as _mg
+    outs = _mg.density_multiscale(cfg, 1, sqrt_p, dk)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(3):
+        _mg.density_multiscale(cfg, 2 + i, sqrt_p, dk, outs)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) / 3 * 1e3
+    res["multiscale_zoom2"] = {"ms_per_hierarchy": ms, "level_cells_per_s": geom.level_cells() / (ms * 1e-3),
+                               "includes": "work-array allocation and cuFFT plan creation per call"}
     return res
 
 

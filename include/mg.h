@@ -61,9 +61,12 @@ typedef enum {
 
 /* MG_FP64: every step in float64.  MG_MIXED: iterative refinement; the
  * residual f - L u, the coarsest-level solve and the update u += e are float64,
- * the correction equation L e = r is solved by inner_cycles float32 V-cycles
- * (smoothing, transfers and coarse-fine ghosts in float32) per outer iteration;
- * the stopping test is the same float64 leaf residual norm. */
+ * the correction equation L e = r is solved by float32 V-cycles (smoothing,
+ * transfers and coarse-fine ghosts in float32): inner_cycles of them in the first
+ * outer iteration; each later one runs just enough cycles to take the float64
+ * residual to half the tolerance at the reduction per cycle the previous outer
+ * iteration achieved, at most inner_cycles (all inner_cycles when tol = 0); the
+ * stopping test is the same float64 leaf residual norm. */
 typedef enum { MG_FP64 = 0, MG_MIXED = 1 } mg_precision;
 
 /* MG_FLAG_NO_GRAPHS: launch every kernel on the stream instead of replaying one
@@ -92,7 +95,8 @@ typedef struct {
   int nu1, nu2;                        /* pre/post smoothing sweeps (paper: 2, 2)       */
   int max_cycles;                      /* V-cycle limit per solve (MG_MIXED: outer     */
                                        /* refinement iterations)                        */
-  int inner_cycles;                    /* MG_MIXED: float32 V-cycles per outer iteration */
+  int inner_cycles;                    /* MG_MIXED: float32 V-cycles of the first outer  */
+                                       /* iteration and the most of any later one        */
   int flags;                           /* MG_FLAG_* bits; 0 = defaults                  */
   int tile_rows;                       /* smoother block: 32 z-pairs x tile_rows y rows  */
                                        /* (1, 2, 4, 8; 0 = 4)                            */

@@ -128,7 +128,9 @@ struct mg_hierarchy {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   // MG_FP64: V-cycle + norm; MG_MIXED: outer iteration + norm.  [0] launches
   // plainly; [1] also records the profiling events (first cycle of each solve).
-  Graph g_cycle[2];
+  // [inner cycles of the body (MG_MIXED; 0 for MG_FP64)][timed]
+  Graph g_cycle[17][2];
+  int inner_now = 0;  // MG_MIXED: float32 V-cycles of the next outer iteration
   Graph* capturing = nullptr;     // graph being captured
   Graph* replayed = nullptr;      // graph whose event pairs await reading
   CfWeights w;
@@ -627,7 +629,7 @@ void destroy_graph(Graph& g) {
 template <typename Body>
 mg_status run_body(mg_hierarchy* h, bool timed, Body body) {
   const unsigned mask = timed ? h->prof_mask : 0u;
-  Graph& g = h->g_cycle[timed && mask ? 1 : 0];
+  Graph& g = h->g_cycle[h->mixed ? h->inner_now : 0][timed && mask ? 1 : 0];
   if (h->cfg.flags & MG_FLAG_NO_GRAPHS) {
     const unsigned keep = h->active_mask;
     h->active_mask = mask;
@@ -701,7 +703,7 @@ mg_status zero_correction(mg_hierarchy* h) {
 
 mg_status mixed_outer_body(mg_hierarchy* h) {
   ST(zero_correction(h));
-  for (int m = 0; m < h->cfg.inner_cycles; ++m) ST(vcycle<float>(h, finest(h)));
+  for (int m = 0; m < h->inner_now; ++m) ST(vcycle<float>(h, finest(h)));
   for (int l = h->base; l <= finest(h); ++l) {
     DevLevel& L = h->L[l];
     KL(MG_K_PROLONG, cells_of(L.G),
@@ -773,8 +775,24 @@ mg_status solve_begin_read(mg_hierarchy* h, SolveState& st) {
     ST(norm_read(h, &rr, &ff, &fs));
     st.local.source_mean = fs / h->volume;
     st.rel = ff > 0.0 ? std::sqrt(rr) / std::sqrt(ff) : std::sqrt(rr);
+    h->inner_now = h->cfg.inner_cycles;
   }
   return MG_OK;
+}
+
+// MG_MIXED: float32 V-cycles for the next outer iteration.  The first one runs
+// inner_cycles; later ones run just enough cycles to take the float64 residual from
+// rel to half the tolerance at the reduction per cycle the previous iteration
+// achieved, at most inner_cycles (the stopping test stays the float64 residual).
+int next_inner_cycles(const mg_hierarchy* h, double rel_before, double rel_after, int used) {
+  const int cap = h->cfg.inner_cycles;
+  if (!(h->cfg.tol > 0.0) || !(rel_after > 0.0) || !(rel_before > rel_after) || used < 1)
+    return cap;
+  const double per_cycle = std::log(rel_before / rel_after) / used;
+  const double need = std::log(rel_after / (0.5 * h->cfg.tol)) / per_cycle;
+  if (!std::isfinite(need)) return cap;
+  const int n = (int)std::ceil(need);
+  return n < 1 ? 1 : (n > cap ? cap : n);
 }
 
 // The launches of one V-cycle (MG_FP64) or one outer iteration (MG_MIXED).
@@ -787,8 +805,12 @@ mg_status solve_step_read(mg_hierarchy* h, SolveState& st) {
   double rr, ff, fs;
   ST(norm_read(h, &rr, &ff, &fs));
   if (st.c == 0 && !h->mixed) st.local.source_mean = fs / h->volume;
-  if (h->mixed) st.local.inner_cycles += h->cfg.inner_cycles;
+  const double before = st.rel;
   st.rel = ff > 0.0 ? std::sqrt(rr) / std::sqrt(ff) : std::sqrt(rr);
+  if (h->mixed) {
+    st.local.inner_cycles += h->inner_now;
+    h->inner_now = next_inner_cycles(h, before, st.rel, h->inner_now);
+  }
   record(st.local, st.rel);
   st.c++;
   const bool fixed = !(h->cfg.tol > 0.0);
@@ -1014,7 +1036,8 @@ struct mg_batch {
   cudaEvent_t ev_in = nullptr, fork = nullptr;
   std::vector<cudaEvent_t> join;   // recorded inside captures only
   std::vector<cudaEvent_t> ready;  // member stream -> batch stream ordering before a replay
-  std::map<std::vector<bool>, BatchGraph> graphs;
+  // per set of active members and their bodies: 0 inactive, else 1 + inner cycles
+  std::map<std::vector<int>, BatchGraph> graphs;
   std::string err;
 };
 
@@ -1039,7 +1062,7 @@ mg_status member_status(mg_batch* b, int i, mg_status st) {
   return st;
 }
 
-mg_status batch_graph(mg_batch* b, const std::vector<bool>& active, BatchGraph** out) {
+mg_status batch_graph(mg_batch* b, const std::vector<int>& active, BatchGraph** out) {
   auto it = b->graphs.find(active);
   if (it != b->graphs.end()) {
     *out = &it->second;
@@ -1100,10 +1123,10 @@ mg_status batch_solve(mg_batch* b, mg_info* infos) {
     if (r != MG_OK) return member_status(b, (int)i, r);
   }
   for (;;) {
-    std::vector<bool> active(n);
+    std::vector<int> active(n);
     bool any = false;
     for (size_t i = 0; i < n; ++i) {
-      active[i] = !st[i].done;
+      active[i] = st[i].done ? 0 : 1 + (b->m[i]->mixed ? b->m[i]->inner_now : 0);
       any = any || active[i];
     }
     if (!any) break;
@@ -1458,8 +1481,10 @@ mg_status mg_hierarchy_create(const mg_config* cfg, void* cuda_stream, mg_hierar
 mg_status mg_hierarchy_destroy(mg_hierarchy* h) {
   if (!h) return MG_OK;
   if (h->s) cudaStreamSynchronize(h->s);
-  destroy_graph(h->g_cycle[0]);
-  destroy_graph(h->g_cycle[1]);
+  for (auto& pair : h->g_cycle) {
+    destroy_graph(pair[0]);
+    destroy_graph(pair[1]);
+  }
   if (h->arena) {
     if (h->cfg.dev_free) h->cfg.dev_free(h->arena, h->cfg.alloc_ctx);
     else cudaFree(h->arena);

@@ -218,7 +218,8 @@ def test_mixed_precision_matches_fp64_oracle(lib, order):
     h = hier(lib, geom, tol=1e-10, precision=lib.MG_MIXED, inner_cycles=2)
     out, i1, i2 = h.pipeline(to_dev(deltas))
     assert i1["rel_residual"] <= 1e-10 and i2["rel_residual"] <= 1e-10
-    assert i1["inner_cycles"] == 2 * i1["cycles"]
+    # first outer iteration: inner_cycles float32 V-cycles; later ones 1..inner_cycles
+    assert 2 + (i1["cycles"] - 1) <= i1["inner_cycles"] <= 2 * i1["cycles"]
     for l in range(geom.n_levels):
         assert rel(out["phi1"][l], ref["phi1"][l]) <= 1e-6
         assert rel(out["phi2"][l], ref["phi2"][l]) <= 1e-6

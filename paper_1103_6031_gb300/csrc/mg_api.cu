@@ -771,10 +771,9 @@ mg_status solve_begin_read(mg_hierarchy* h, SolveState& st) {
   st.done = false;
   st.rel = INFINITY;
   if (h->mixed) {
-    double rr, ff, fs;
-    ST(norm_read(h, &rr, &ff, &fs));
-    st.local.source_mean = fs / h->volume;
-    st.rel = ff > 0.0 ? std::sqrt(rr) / std::sqrt(ff) : std::sqrt(rr);
+    // with u = 0 the first residual is the source itself (relative norm 1): no host
+    // read here; the source mean arrives with the first iteration's norm
+    st.rel = 1.0;
     h->inner_now = h->cfg.inner_cycles;
   }
   return MG_OK;
@@ -804,7 +803,7 @@ mg_status solve_body(mg_hierarchy* h) {
 mg_status solve_step_read(mg_hierarchy* h, SolveState& st) {
   double rr, ff, fs;
   ST(norm_read(h, &rr, &ff, &fs));
-  if (st.c == 0 && !h->mixed) st.local.source_mean = fs / h->volume;
+  if (st.c == 0) st.local.source_mean = fs / h->volume;
   const double before = st.rel;
   st.rel = ff > 0.0 ? std::sqrt(rr) / std::sqrt(ff) : std::sqrt(rr);
   if (h->mixed) {

@@ -100,7 +100,9 @@ typedef struct {
   int flags;                           /* MG_FLAG_* bits; 0 = defaults                  */
   int tile_rows;                       /* smoother block: 32 z-pairs x tile_rows y rows  */
                                        /* (1, 2, 4, 8; 0 = 4)                            */
-  double tol;                          /* stop when leaf |r| / leaf |f| <= tol          */
+  double tol;                          /* stop when leaf |r| / leaf |f| <= tol, or when  */
+                                       /* |r| <= 64 eps (|f|^2 + V mean^2)^(1/2), the     */
+                                       /* rounding level of a constant source             */
   void* (*dev_alloc)(size_t bytes, void* ctx);
   void (*dev_free)(void* ptr, void* ctx);
   void* alloc_ctx;

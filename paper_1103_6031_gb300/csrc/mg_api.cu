@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cfloat>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -732,12 +733,14 @@ mg_status remove_source_mean(mg_hierarchy* h) {
   return MG_OK;
 }
 
-mg_status finish_info(mg_hierarchy* h, mg_info& local, double rel, mg_info* info) {
+mg_status finish_info(mg_hierarchy* h, mg_info& local, double rel, bool at_floor,
+                      mg_info* info) {
   local.rel_residual = rel;
   if (info) *info = local;
   const bool fixed = !(h->cfg.tol > 0.0);
   if (!std::isfinite(rel)) return fail(h, MG_ENOCONV, "residual is not finite");
-  if (!fixed && rel > h->cfg.tol) return fail(h, MG_ENOCONV, "max_cycles reached above tol");
+  if (!fixed && rel > h->cfg.tol && !at_floor)
+    return fail(h, MG_ENOCONV, "max_cycles reached above tol");
   return MG_OK;
 }
 
@@ -753,6 +756,7 @@ struct SolveState {
   double rel = INFINITY;
   int c = 0;
   bool done = false;
+  bool at_floor = false;  // residual at the rounding level of the source (see below)
 };
 
 // Queues the set-up: composite mean removal, zero solution, tangential caches
@@ -813,7 +817,14 @@ mg_status solve_step_read(mg_hierarchy* h, SolveState& st) {
   record(st.local, st.rel);
   st.c++;
   const bool fixed = !(h->cfg.tol > 0.0);
-  st.done = !std::isfinite(st.rel) || (!fixed && st.rel <= h->cfg.tol) ||
+  // A source that is constant up to rounding (zero after the mean removal but for
+  // its rounding) has no meaningful relative residual: the solve stops once the
+  // residual is at the rounding level of the source before the mean removal,
+  // 64 eps (|f|^2 + V mean^2)^{1/2} (volume-weighted; the solution is then ~0).
+  const double mean = st.local.source_mean;
+  const double floor = 64.0 * DBL_EPSILON * std::sqrt(ff + h->volume * mean * mean);
+  st.at_floor = !fixed && std::sqrt(rr) <= floor;
+  st.done = !std::isfinite(st.rel) || (!fixed && st.rel <= h->cfg.tol) || st.at_floor ||
             st.c >= h->cfg.max_cycles;
   return MG_OK;
 }
@@ -843,7 +854,7 @@ mg_status gauge_zero_base_mean(mg_hierarchy* h) {
 }
 
 mg_status solve_end(mg_hierarchy* h, SolveState& st, mg_info* info) {
-  const mg_status res = finish_info(h, st.local, st.rel, info);
+  const mg_status res = finish_info(h, st.local, st.rel, st.at_floor, info);
   if (res != MG_OK && res != MG_ENOCONV) return res;
   if (h->mixed) ST(gauge_zero_base_mean(h));
   return res;

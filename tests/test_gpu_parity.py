@@ -269,3 +269,25 @@ def test_deep_zoom_full_size(lib):
     for key in ("phi1", "phi2", "disp1", "disp2"):
         for x, y in zip(a[key], b[key]):
             assert rel(x, y.cpu().numpy()) <= 1e-6, key
+
+
+@pytest.mark.parametrize("mixed", [False, True], ids=["fp64", "mixed"])
+def test_zero_and_constant_sources(lib, mixed):
+    """Degenerate sources: zero, and a constant (which the composite mean removal
+    makes zero up to rounding): the first solve stops after one cycle at the
+    rounding-level floor with phi ~ 0; tau ~ 0; no NaN anywhere, status OK."""
+    import torch
+    geom = small_zoom(24, ((20, 7),), order=6, box=50.0)
+    kw = dict(tol=1e-10)
+    if mixed:
+        kw.update(precision=lib.MG_MIXED, inner_cycles=2)
+    h = hier(lib, geom, **kw)
+    shapes = h.shapes
+    for value in (0.0, 3.5):
+        d = [torch.full(s, value, dtype=torch.float64, device="cuda") for s in shapes]
+        out, i1, i2 = h.pipeline(d)
+        assert i1["cycles"] == 1
+        for key in ("phi1", "phi2", "disp1", "disp2"):
+            for x in out[key]:
+                assert torch.isfinite(x).all() and x.abs().max().item() < 1e-12, key
+        assert abs(i1["source_mean"] - value) < 1e-12

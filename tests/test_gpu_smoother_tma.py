@@ -102,3 +102,21 @@ def test_smoother_kernels_bench_workload_bit_identical(lib):
     for key in ("phi1", "phi2", "disp1", "disp2"):
         for x, y in zip(a[key], b[key]):
             assert torch.equal(x, y), key
+
+
+def test_tma_default_on_a_256_cube_nest_bit_identical(lib):
+    """The size class the TMA-staged kernel is the default for: a 256^3 float32 nest
+    (inside a 256^3 periodic base), mixed precision, order 6, against the plain kernel."""
+    import torch
+    from synthetic import Geometry, NestSpec
+    geom = Geometry((256, 256, 256), 200.0, 6, (NestSpec((256, 256, 256), (64, 64, 64)),))
+    rng = np.random.Generator(np.random.PCG64(8))
+    deltas = [rng.standard_normal((256,) * 3), rng.standard_normal((256,) * 3)]
+    kw = dict(tol=1e-7, max_cycles=30, precision=lib.MG_MIXED, inner_cycles=4)
+    a, ai1, ai2 = run(lib, geom, deltas, "off", **kw)
+    b, bi1, bi2 = run(lib, geom, deltas, "auto", **kw)
+    assert ai1["cycles"] == bi1["cycles"] and ai2["cycles"] == bi2["cycles"]
+    assert ai1["rel_residual"] <= 1e-7
+    for key in ("phi1", "phi2", "disp1", "disp2"):
+        for x, y in zip(a[key], b[key]):
+            assert torch.equal(x, y), key

@@ -9,7 +9,7 @@ import re
 import pytest
 
 from oracle.hierarchy import Hierarchy as OracleHierarchy
-from synthetic import Geometry, NestSpec, config_batch, config_deep_zoom, config_zoom2, small_zoom
+from synthetic import Geometry, config_batch, config_deep_zoom, config_zoom2, small_zoom
 
 
 @pytest.fixture(scope="module")

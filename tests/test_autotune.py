@@ -1,9 +1,8 @@
 """Autotuner host logic (CPU) and one tuning run on the GPU."""
 
-import numpy as np
 import pytest
 
-from synthetic import Geometry, config_batch, make_delta, small_zoom
+from synthetic import config_batch, make_delta, small_zoom
 
 
 @pytest.fixture(scope="module")

@@ -11,7 +11,7 @@ from oracle.hierarchy import Hierarchy as OracleHierarchy
 from oracle.hierarchy import restrict
 from oracle.hybrid import hybrid_correction
 from oracle.lpt import lpt2_source
-from oracle.multigrid import composite_mean, solve
+from oracle.multigrid import composite_mean
 from synthetic import Geometry, make_delta, small_zoom
 
 pytestmark = pytest.mark.gpu

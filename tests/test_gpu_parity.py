@@ -185,7 +185,6 @@ def test_errors_are_reported(lib):
     assert e.value.status == 3  # MG_ENOCONV
     phis, info = h.solve_1lpt(deltas, allow_noconv=True)
     assert info["cycles"] == 1 and np.isfinite(phis[0].cpu().numpy()).all()
-    import ctypes
     st = h.lib.mg_solve_1lpt(h.h, None, None, None)
     assert st == 1
 

@@ -20,8 +20,7 @@ import numpy as np
 import pytest
 
 from oracle.fft_solve import exact_solve, spectral_gradient
-from oracle.hierarchy import (Hierarchy, fill_ghosts, fill_periodic, inject, laplacian,
-                              restrict)
+from oracle.hierarchy import Hierarchy, fill_ghosts, inject, laplacian
 from oracle.lpt import gradient
 from oracle.multigrid import leaf_residual_norms, solve, sync_covered
 from oracle.stencils import FLUX_1D

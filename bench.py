@@ -41,7 +41,7 @@ MIXED_INNER_CYCLES = 4
 # V-cycles of one full step (1LPT + 2LPT; unigrid64: 1LPT) at each workload's
 # stopping rule, as the GPU arm reports them; the oracle arm scales its one-cycle
 # sample by this.
-CYCLES_PER_STEP = {"zoom2": 14, "unigrid64": 9, "deep_zoom": 14}
+CYCLES_PER_STEP = {"zoom2": 14, "unigrid64": 9, "deep_zoom": 14, "zoom256": 14}
 FP64_PEAK_GOPS = 625.0   # nominal 1.25 TFLOP/s FP64 = 625 G FP64 instructions/s
 HBM_PEAK_GBS = 6765.0    # measured copy bandwidth of the GB300s
 L2_FLUSH_BYTES = 256 << 20
@@ -60,9 +60,10 @@ SMOOTH_TRAFFIC_PER_UPDATE = 35.8
 
 # Workloads: zoom2 is the headline; the others are the single-level and deep-zoom
 # configurations, measured with --workload.  Seeds and stopping rules per workload.
-WORKLOADS = ("zoom2", "unigrid64", "deep_zoom")
-WORKLOAD_SEED = {"zoom2": SEED, "unigrid64": 1, "deep_zoom": 3}
-WORKLOAD_TOL = {"zoom2": SOLVE_TOL, "unigrid64": 1e-10, "deep_zoom": SOLVE_TOL}
+WORKLOADS = ("zoom2", "unigrid64", "deep_zoom", "zoom256")
+WORKLOAD_SEED = {"zoom2": SEED, "unigrid64": 1, "deep_zoom": 3, "zoom256": 4}
+WORKLOAD_TOL = {"zoom2": SOLVE_TOL, "unigrid64": 1e-10, "deep_zoom": SOLVE_TOL,
+                "zoom256": SOLVE_TOL}
 WORKLOAD_TEXT = {
     "zoom2": "zoom2: 128^3 periodic base (100 Mpc/h) + centred 128^3 nest at 2x, order-6 FD, "
              "FP64, 1LPT+2LPT+displacements, BBKS z=50, seed 2",
@@ -70,13 +71,16 @@ WORKLOAD_TEXT = {
                  "to 1e-10 relative residual, power law P ~ k^-2 at unit RMS, seed 1",
     "deep_zoom": "deep zoom: 128^3 periodic base (100 Mpc/h) + 4 nests of 128^3, centred with "
                  "+-16 jitter (seed 3), order-6 FD, FP64, 1LPT+2LPT+displacements, BBKS z=50",
+    "zoom256": "zoom256: 256^3 periodic base (200 Mpc/h) + centred 256^3 nest at 2x, order-6 FD, "
+               "FP64, 1LPT+2LPT+displacements, BBKS z=50, seed 4 (the size of the serving "
+               "configuration's large levels; its float32 nest takes the TMA-staged smoother)",
 }
 
 
 def workload(name="zoom2"):
     from synthetic import config_deep_zoom, config_unigrid64, config_zoom2
-    return {"zoom2": config_zoom2, "unigrid64": config_unigrid64,
-            "deep_zoom": config_deep_zoom}[name]()
+    return {"zoom2": config_zoom2, "unigrid64": config_unigrid64, "deep_zoom": config_deep_zoom,
+            "zoom256": lambda: config_zoom2(base=256, nest=256, box=200.0)}[name]()
 
 
 def workload_inputs(name, geom):

@@ -207,6 +207,69 @@ def cpu_baseline(geom, deltas, cycles_per_step, lpt2=True):
                       % (t_cycle, t_tau, t_grad, cycles_per_step, rest)}
 
 
+_BARRIER = None
+
+
+def _oracle_worker_init(barrier):
+    global _BARRIER
+    _BARRIER = barrier
+
+
+def _oracle_worker(name):
+    """One process of the all-cores oracle run: builds the workload's inputs, waits
+    for every other process, then times the same sample as cpu_baseline."""
+    from oracle.hierarchy import Hierarchy
+    from oracle.lpt import gradient, lpt2_source
+    from oracle.multigrid import solve
+    geom = workload(name)
+    deltas = workload_inputs(name, geom)
+    _BARRIER.wait(timeout=600)  # a process that failed breaks the barrier for all
+    t0 = time.perf_counter()
+    phis, _ = solve(geom, deltas, tol=0.0, cycles=1)
+    t1 = time.perf_counter()
+    if name != "unigrid64":
+        lpt2_source(Hierarchy(geom), phis)
+    t2 = time.perf_counter()
+    gradient(Hierarchy(geom), phis)
+    t3 = time.perf_counter()
+    return t1 - t0, t2 - t1, t3 - t2
+
+
+def cpu_baseline_all_cores(name, geom, cycles_per_step, lpt2=True):
+    """The oracle on every host core: one process per core (spawned, one thread
+    each), each timing the cpu_baseline sample on its own copy of the hierarchy at
+    the same moment; value = processes x level-cells / the slowest process's
+    scaled step time."""
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in env:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        barrier = ctx.Barrier(cores)
+        t0 = time.perf_counter()
+        with ctx.Pool(cores, initializer=_oracle_worker_init, initargs=(barrier,)) as pool:
+            times = pool.map(_oracle_worker, [name] * cores, chunksize=1)
+        wall = time.perf_counter() - t0
+    finally:
+        for k, v in env.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    t_cycle = max(t[0] for t in times)
+    t_tau = max(t[1] for t in times)
+    t_grad = max(t[2] for t in times)
+    t_step = cycles_per_step * t_cycle + (t_tau + 2 * t_grad if lpt2 else t_grad)
+    return {"value": cores * geom.level_cells() / t_step, "unit": UNIT, "cores": cores,
+            "kind": "oracle",
+            "sample": "%d processes (one per host core, one thread each) each timing 1 V-cycle "
+                      "(slowest %.1f s) + tau (%.1f s) + 1 gradient (%.1f s) of its own copy of "
+                      "the hierarchy at once, scaled like the one-core figure (%.0f s wall with "
+                      "input generation)" % (cores, t_cycle, t_tau, t_grad, wall)}
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -760,8 +823,11 @@ def run_ours(args):
                     "ms_per_step": statistics.mean(e2e_ms)},
         }
         if not args.skip_baseline and world == 1:
-            line["cpu_baseline"] = cpu_baseline(
-                geom, deltas_np, info1["cycles"] + (info2["cycles"] if info2 else 0), lpt2)
+            cycles = info1["cycles"] + (info2["cycles"] if info2 else 0)
+            line["cpu_baseline"] = cpu_baseline(geom, deltas_np, cycles, lpt2)
+            if not args.skip_all_cores:
+                line["cpu_baseline"]["all_cores"] = cpu_baseline_all_cores(
+                    args.workload, geom, cycles, lpt2)
         print(json.dumps(line))
     h.close()
     if dist is not None:
@@ -776,9 +842,11 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=WORKLOADS, default="zoom2",
-                    help="zoom2 (default, the headline), unigrid64 or deep_zoom")
+                    help="zoom2 (default, the headline), unigrid64, deep_zoom or zoom256")
     ap.add_argument("--skip-baseline", action="store_true",
                     help="leave out the CPU-oracle baseline")
+    ap.add_argument("--skip-all-cores", action="store_true",
+                    help="leave out the all-cores run of the CPU-oracle baseline")
     ap.add_argument("--profile-run", action="store_true",
                     help="timed steps only: no end-to-end pass, no CPU baseline (for ncu)")
     ap.add_argument("--no-batch", action="store_true",

@@ -64,9 +64,10 @@ typedef enum {
  * the correction equation L e = r is solved by float32 V-cycles (smoothing,
  * transfers and coarse-fine ghosts in float32): inner_cycles of them in the first
  * outer iteration; each later one runs just enough cycles to take the float64
- * residual to half the tolerance at the reduction per cycle the previous outer
- * iteration achieved, at most inner_cycles (all inner_cycles when tol = 0); the
- * stopping test is the same float64 leaf residual norm. */
+ * residual to a quarter of the tolerance at the reduction the previous outer
+ * iteration achieved (its first cycle, from a zero correction, counted as 5 times
+ * weaker than the others), at most inner_cycles (all inner_cycles when tol = 0);
+ * the stopping test is the same float64 leaf residual norm. */
 typedef enum { MG_FP64 = 0, MG_MIXED = 1 } mg_precision;
 
 /* MG_FLAG_NO_GRAPHS: launch every kernel on the stream instead of replaying one

@@ -349,10 +349,12 @@ def batch_inputs(large_side=None):
     return geoms, deltas[:len(geoms)], large
 
 
-def serving_measure(pkg, geoms, deltas_np, large, seconds, rate, workers):
+def serving_measure(pkg, geoms, deltas_np, large, seconds, rate, workers, native=True):
     """Open-loop Poisson arrivals (mean `rate`/s for `seconds`): 90% draws from the
     batched workload's hierarchies, 10% the large class; mixed precision, host
-    buffers in and out, admission by HBM budget, device-resident hierarchies."""
+    buffers in and out, admission by HBM budget, device-resident hierarchies.
+    native: the C++ scheduler (mg_server_*, `workers` requests on the GPU at
+    once); else the Python server with `workers` threads."""
     import numpy as np
     import torch
     from paper_1103_6031_gb300 import serve
@@ -374,7 +376,10 @@ def serving_measure(pkg, geoms, deltas_np, large, seconds, rate, workers):
             reqs.append(serve.Request(k, cfg_small[i], pinned[i]))
             reqs[-1].cls = "batch_draw"
             cells += geoms[i].level_cells()
-    server = serve.Server(workers=workers, hbm_budget=64 << 30, keep_outputs=False)
+    if native:
+        server = serve.NativeServer(max_active=workers, hbm_budget=64 << 30, keep_outputs=False)
+    else:
+        server = serve.Server(workers=workers, hbm_budget=64 << 30, keep_outputs=False)
     # warm server: one untimed request per configuration first, so that the timed
     # window sees resident hierarchies with captured graphs (steady state), not the
     # first-use allocation and capture of 65 configurations
@@ -388,6 +393,11 @@ def serving_measure(pkg, geoms, deltas_np, large, seconds, rate, workers):
     server.completed.clear()
     wall = serve.run_open_loop(server, reqs, rate, seed=SERVE_SEED)
     errors = [r for r in reqs if r.error is not None]
+    if native:
+        st = server.stats()
+        peak_gb, evictions = st["peak_bytes"] / 2 ** 30, st["evictions"]
+    else:
+        peak_gb, evictions = server.admission.peak / 2 ** 30, server.admission.evictions
     stats = serve.latency_stats(reqs)
     by_class = {}
     for c in ("batch_draw", "large"):
@@ -400,11 +410,12 @@ def serving_measure(pkg, geoms, deltas_np, large, seconds, rate, workers):
            "latency_ms": {"p50": stats["p50_ms"], "p99": stats["p99_ms"], "mean": stats["mean_ms"],
                           "max": stats["max_ms"]},
            "latency_ms_by_class": by_class,
+           "server": ("native: one C++ scheduler thread, non-blocking pipelines (mg_server_*)"
+                      if native else "python: one thread per request in flight"),
            "workers": workers, "peak_inflight": server.peak_inflight,
            "warmup": {"requests": len(warm), "seconds": warm_s,
                       "what": "one untimed request per configuration before the timed window"},
-           "peak_resident_gb": server.admission.peak / 2 ** 30,
-           "evictions": server.admission.evictions, "errors": len(errors),
+           "peak_resident_gb": peak_gb, "evictions": evictions, "errors": len(errors),
            "mix": "90%% draws from the 64 batched hierarchies, 10%% %d^3 base + 3 nests of %d^3 "
                   "(%.1f M level-cells); mixed precision; pinned host buffers in and out; "
                   "latency from arrival to results in host memory" % (
@@ -659,7 +670,8 @@ def run_ours(args):
     serving = None
     if batch is not None and args.serve_seconds > 0 and world == 1:
         serving = serving_measure(pkg, batch[0], batch[1], batch[2], args.serve_seconds,
-                                  args.serve_rate, args.serve_workers)
+                                  args.serve_rate, args.serve_workers,
+                                  native=args.serve_impl == "native")
     all_ms = sa["event_ms"] / max(sa["timed"], 1)
     all_updates = sa["timed_cells"] / max(sa["timed"], 1)
     all_gops = SMOOTH_OPS_PER_UPDATE[geom.order] * all_updates / (all_ms * 1e-3) / 1e9
@@ -854,7 +866,9 @@ def main(argv=None):
     ap.add_argument("--serve-seconds", type=float, default=5.0,
                     help="seconds of open-loop arrivals in the serving measurement (0: none)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="mean arrivals per second")
-    ap.add_argument("--serve-workers", type=int, default=6, help="concurrent requests at most")
+    ap.add_argument("--serve-workers", type=int, default=16, help="concurrent requests at most")
+    ap.add_argument("--serve-impl", choices=["native", "python"], default="native",
+                    help="serving runtime: the C++ scheduler (mg_server_*) or Python threads")
     ap.add_argument("--serve-large-side", type=int, default=128,
                     help="side of the large request class (base and 3 nests); 256 is full size")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",

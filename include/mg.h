@@ -243,6 +243,77 @@ mg_status mg_batch_lpt_pipeline(mg_batch* b, int host_buffers, const double* con
 /* Message for the last failing batch call ("" if none; NULL-safe). */
 const char* mg_batch_last_error(const mg_batch* b);
 
+/* Serving runtime: a request queue in front of resident hierarchies, driven by
+ * one native scheduler thread.  A request is mg_lpt_pipeline(host_buffers = 1)
+ * for one configuration: the density delta in (preferably pinned) host memory
+ * in, phi1, phi2 and both displacement fields out to host memory.
+ *  - Admission by HBM budget: a request needs mg_workspace_bytes(cfg) of device
+ *    memory for a hierarchy of its configuration; the server keeps the bytes of
+ *    its resident hierarchies under the budget, closing idle ones (least
+ *    recently used first) to make room.  Each scheduler pass first starts, in
+ *    arrival order, the pending requests that find an idle resident hierarchy
+ *    of their configuration, then gives the oldest request still waiting a new
+ *    hierarchy if it fits (one creation per pass).
+ *  - Resident state: hierarchies are cached by configuration (every field of
+ *    mg_config), so a repeated configuration reuses its levels and captured
+ *    CUDA graphs; overlapping requests of one configuration get one hierarchy
+ *    each, budget permitting.
+ *  - Overlap without a thread per request: each admitted request runs as a
+ *    non-blocking job on its hierarchy's stream; the scheduler polls the event
+ *    after the work a job queued last and queues the job's next piece (next
+ *    iteration, tau, stores) when it has finished, so up to max_active requests
+ *    at different stages share the GPU.
+ *  - Results depend only on the request: the same launches as mg_lpt_pipeline
+ *    on the same data, so they are bit-identical to a solo call.
+ * The device is the one current when mg_server_create is called.  The server
+ * owns its hierarchies; the caller owns every buffer of a request, which must
+ * stay valid until the request's result has been returned by mg_server_poll. */
+typedef struct mg_server mg_server;
+
+typedef struct {
+  long long id;        /* the id given to mg_server_submit                         */
+  int status;          /* mg_status of the request's pipeline                      */
+  mg_info info1, info2;/* convergence records of the 1LPT and 2LPT solves          */
+  double t_submit;     /* CLOCK_MONOTONIC seconds: submitted, started on the GPU,   */
+  double t_start;      /* results in host memory                                  */
+  double t_done;
+  char error[160];     /* message of a failed request ("" otherwise)               */
+} mg_server_result;
+
+typedef struct {
+  unsigned long long resident_bytes;  /* mg_workspace_bytes of resident hierarchies */
+  unsigned long long peak_bytes;
+  unsigned long long budget_bytes;
+  long long created;                  /* hierarchies created                        */
+  long long evictions;                /* idle hierarchies closed to make room        */
+  long long completed;                /* results handed to the result queue          */
+  int pending, active, instances, peak_active;
+} mg_server_stats;
+
+/* max_active: requests on the GPU at once (1..256).  Errors: MG_EINVAL, MG_ECUDA. */
+mg_status mg_server_create(unsigned long long hbm_budget, int max_active, mg_server** out);
+
+/* Queues one request.  delta: one host pointer per leaf level (base first, dense
+ * [nx][ny][nz] float64); phi1, phi2: NULL or one host pointer per leaf level;
+ * disp1, disp2: NULL or three per leaf level (x, y, z).  The pointer arrays are
+ * copied.  Returns MG_EINVAL (invalid cfg, missing pointers, server closing) or
+ * MG_ENOMEM (the hierarchy alone exceeds the budget) without queueing it. */
+mg_status mg_server_submit(mg_server* s, long long id, const mg_config* cfg,
+                           const double* const delta[], double* const phi1[],
+                           double* const phi2[], double* const disp1[], double* const disp2[]);
+
+/* Moves up to max finished requests' results into out (completion order),
+ * waiting up to wait_seconds for the first one; returns how many (0 on timeout,
+ * -1 for invalid arguments). */
+int mg_server_poll(mg_server* s, mg_server_result* out, int max, double wait_seconds);
+
+mg_status mg_server_get_stats(mg_server* s, mg_server_stats* out);
+
+/* Stops taking requests, fails the ones not yet started (status MG_EINVAL,
+ * "server closed"), waits for the running ones, frees every hierarchy.
+ * NULL-safe.  Results not yet polled are dropped. */
+mg_status mg_server_destroy(mg_server* s);
+
 /* Kernel families for launch counting and event timing. */
 typedef enum {
   MG_K_SMOOTH = 0,     /* red-black half-sweep                                 */

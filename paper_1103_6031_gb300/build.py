@@ -71,7 +71,7 @@ def build(force=False, verbose=False, extra=()):
     tmp = LIB + ".tmp"
     cudalib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(shutil.which(_nvcc()) or _nvcc()))), "lib64")
     cmd = [_nvcc()] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results] + \
-        ["-lcufft", "-Xlinker", "-rpath=" + cudalib]
+        ["-lcufft", "-lpthread", "-Xlinker", "-rpath=" + cudalib]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), res.stderr))

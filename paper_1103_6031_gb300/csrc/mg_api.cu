@@ -1219,6 +1219,166 @@ mg_status batch_pipeline(mg_batch* b, bool host, const double* const* const delt
 
 }  // namespace
 
+// ---- non-blocking pipeline jobs (the serving runtime) ---------------------------
+//
+// mg_lpt_pipeline with host buffers as a state machine that never waits for the
+// GPU: job_poll only looks at the event recorded after the work it queued last,
+// and once that work has finished it reads the convergence record and queues the
+// next piece (the next iteration, the stores and tau between the solves, the
+// final stores).  One host thread can so drive the pipelines of many hierarchies,
+// each on its own stream, with the same launches as mg_lpt_pipeline.
+
+namespace mgk {
+
+struct PipelineJob {
+  mg_hierarchy* h = nullptr;
+  std::vector<const double*> delta;
+  std::vector<double*> phi1, phi2, disp1, disp2;  // empty: not requested
+  int phase = 0;  // 1, 2: solve 1, 2 running; 3: final copies queued; 4: finished
+  SolveState st;
+  mg_info info[2];
+  mg_status res[2] = {MG_OK, MG_OK};
+  mg_status status = MG_OK;
+  cudaEvent_t ev = nullptr;
+};
+
+namespace {
+
+mg_status job_record(PipelineJob* j) {
+  mg_hierarchy* h = j->h;
+  CK(cudaEventRecord(j->ev, h->s));
+  return MG_OK;
+}
+
+// Queues the set-up and the first iteration of a solve whose source is in f.
+mg_status job_begin_solve(PipelineJob* j) {
+  mg_hierarchy* h = j->h;
+  ST(solve_begin(h));
+  ST(solve_begin_read(h, j->st));
+  ST(run_body(h, true, solve_body));
+  return job_record(j);
+}
+
+mg_status job_store(PipelineJob* j, const std::vector<double*>& phi,
+                    const std::vector<double*>& disp) {
+  mg_hierarchy* h = j->h;
+  if (!phi.empty())
+    for (int l = h->base; l <= finest(h); ++l)
+      ST(store_leaf(h, l, phi_of(h->L[l]), phi[l - h->base], true));
+  if (!disp.empty()) ST(gradient_out(h, const_cast<double* const*>(disp.data()), true, true));
+  return MG_OK;
+}
+
+// The iteration queued last has finished: read it and queue what comes next.
+mg_status job_advance(PipelineJob* j) {
+  mg_hierarchy* h = j->h;
+  ST(solve_step_read(h, j->st));  // its stream synchronisation returns at once
+  if (!j->st.done) {
+    ST(run_body(h, false, solve_body));
+    return job_record(j);
+  }
+  const int k = j->phase - 1;
+  const mg_status e = solve_end(h, j->st, &j->info[k]);
+  if (e != MG_OK && e != MG_ENOCONV) return e;
+  j->res[k] = e;
+  if (j->phase == 1) {
+    ST(job_store(j, j->phi1, j->disp1));
+    ST(tau_into_f(h));
+    j->phase = 2;
+    return job_begin_solve(j);
+  }
+  ST(job_store(j, j->phi2, j->disp2));
+  j->phase = 3;
+  return job_record(j);
+}
+
+void job_finish(PipelineJob* j, mg_status st) {
+  if (st != MG_OK) {
+    // nothing may still write the caller's buffers once the job reports
+    cudaStreamSynchronize(j->h->s);
+    j->status = st;
+  } else {
+    j->status = j->res[0] != MG_OK ? j->res[0] : j->res[1];
+  }
+  j->phase = 4;
+}
+
+bool ptr_array(const double* const* p, int count, bool required) {
+  if (!p) return !required;
+  for (int i = 0; i < count; ++i)
+    if (!p[i]) return false;
+  return true;
+}
+
+}  // namespace
+
+mg_status job_start(mg_hierarchy* h, const double* const delta[], double* const phi1[],
+                    double* const phi2[], double* const disp1[], double* const disp2[],
+                    PipelineJob** out) {
+  *out = nullptr;
+  const int nleaf = n_leaf(h);
+  if (!ptr_array(delta, nleaf, true) || !ptr_array(phi1, nleaf, false) ||
+      !ptr_array(phi2, nleaf, false) || !ptr_array(disp1, 3 * nleaf, false) ||
+      !ptr_array(disp2, 3 * nleaf, false))
+    return fail(h, MG_EINVAL, "delta needs one pointer per level; each output NULL or full");
+  PipelineJob* j = new PipelineJob();
+  j->h = h;
+  j->delta.assign(delta, delta + nleaf);
+  if (phi1) j->phi1.assign(phi1, phi1 + nleaf);
+  if (phi2) j->phi2.assign(phi2, phi2 + nleaf);
+  if (disp1) j->disp1.assign(disp1, disp1 + 3 * nleaf);
+  if (disp2) j->disp2.assign(disp2, disp2 + 3 * nleaf);
+  const cudaError_t e = cudaEventCreateWithFlags(&j->ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    delete j;
+    return fail_cuda(h, e, "cudaEventCreateWithFlags");
+  }
+  *out = j;
+  mg_status st = MG_OK;
+  for (int l = h->base; l <= finest(h) && st == MG_OK; ++l)
+    st = load_leaf(h, l, j->delta[l - h->base], h->L[l].f, true);
+  j->phase = 1;
+  if (st == MG_OK) st = job_begin_solve(j);
+  if (st != MG_OK) job_finish(j, st);
+  return MG_OK;
+}
+
+int job_poll(PipelineJob* j) {
+  if (j->phase == 4) return 2;
+  const cudaError_t q = cudaEventQuery(j->ev);
+  if (q == cudaErrorNotReady) return 0;
+  if (q != cudaSuccess) {
+    job_finish(j, fail_cuda(j->h, q, "cudaEventQuery"));
+    return 2;
+  }
+  if (j->phase == 3) {
+    job_finish(j, MG_OK);
+    return 2;
+  }
+  const mg_status st = job_advance(j);
+  if (st != MG_OK) {
+    job_finish(j, st);
+    return 2;
+  }
+  return 1;
+}
+
+mg_status job_result(const PipelineJob* j, mg_info* info1, mg_info* info2) {
+  if (info1) *info1 = j->info[0];
+  if (info2) *info2 = j->info[1];
+  return j->status;
+}
+
+const char* job_error(const PipelineJob* j) { return j->h->err.c_str(); }
+
+void job_destroy(PipelineJob* j) {
+  if (!j) return;
+  if (j->ev) cudaEventDestroy(j->ev);
+  delete j;
+}
+
+}  // namespace mgk
+
 // ---- C ABI -------------------------------------------------------------------
 
 extern "C" {

@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "mg.h"
+
 namespace mgk {
 
 struct Grid {
@@ -165,5 +167,23 @@ void hybrid_destroy(HybridFFT* hy);
 cudaError_t hybrid_apply(HybridFFT* hy, const double* f, double* const psi[3], cudaStream_t s);
 // device bytes of hybrid_create for that level (buffers and an estimate of cuFFT's work area)
 size_t hybrid_bytes(int n0, int n1, int n2, bool pad);
+
+// ---- non-blocking pipelines (mg_api.cu), driven by the server (mg_serve.cu) ----
+// mg_lpt_pipeline(host_buffers = 1) on h as a job that never waits for the GPU:
+// job_start queues the loads and the first iteration; job_poll advances the job
+// when the work it queued last has finished: it returns 0 (still waiting), 1 (the
+// next piece is queued) or 2 (finished: every result is in the caller's host
+// buffers and nothing is in flight).
+// The pointer arrays are copied; the buffers must stay valid until then.  The
+// hierarchy serves one job at a time.  job_start returns MG_EINVAL (and makes no
+// job) for missing pointers; a job that fails later finishes with that status.
+struct PipelineJob;
+mg_status job_start(mg_hierarchy* h, const double* const delta[], double* const phi1[],
+                    double* const phi2[], double* const disp1[], double* const disp2[],
+                    PipelineJob** out);
+int job_poll(PipelineJob* j);
+mg_status job_result(const PipelineJob* j, mg_info* info1, mg_info* info2);
+const char* job_error(const PipelineJob* j);
+void job_destroy(PipelineJob* j);
 
 }  // namespace mgk

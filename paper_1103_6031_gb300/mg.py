@@ -63,6 +63,37 @@ class MGInfo(ctypes.Structure):
                 "history": [self.history[i] for i in range(min(self.cycles, MG_MAX_HISTORY))]}
 
 
+class MGServerResult(ctypes.Structure):
+    _fields_ = [
+        ("id", ctypes.c_longlong),
+        ("status", ctypes.c_int),
+        ("info1", MGInfo),
+        ("info2", MGInfo),
+        ("t_submit", ctypes.c_double),
+        ("t_start", ctypes.c_double),
+        ("t_done", ctypes.c_double),
+        ("error", ctypes.c_char * 160),
+    ]
+
+
+class MGServerStats(ctypes.Structure):
+    _fields_ = [
+        ("resident_bytes", ctypes.c_ulonglong),
+        ("peak_bytes", ctypes.c_ulonglong),
+        ("budget_bytes", ctypes.c_ulonglong),
+        ("created", ctypes.c_longlong),
+        ("evictions", ctypes.c_longlong),
+        ("completed", ctypes.c_longlong),
+        ("pending", ctypes.c_int),
+        ("active", ctypes.c_int),
+        ("instances", ctypes.c_int),
+        ("peak_active", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 MG_K_FAMILIES = 9
 FAMILY_NAMES = ["smooth", "restrict", "fas", "prolong", "ghost", "coarsest", "norm", "lpt", "copy"]
 
@@ -143,6 +174,13 @@ def load_library(path=None):
         "mg_density_multiscale": (ctypes.c_int, [ctypes.POINTER(MGConfig), ctypes.c_ulonglong,
                                                  ctypes.POINTER(ctypes.c_double), ctypes.c_int,
                                                  ctypes.c_double, ctypes.POINTER(vp), vp]),
+        "mg_server_create": (ctypes.c_int, [ctypes.c_ulonglong, ctypes.c_int, ctypes.POINTER(vp)]),
+        "mg_server_submit": (ctypes.c_int, [vp, ctypes.c_longlong, ctypes.POINTER(MGConfig), pp, pp, pp,
+                                            pp, pp]),
+        "mg_server_poll": (ctypes.c_int, [vp, ctypes.POINTER(MGServerResult), ctypes.c_int,
+                                          ctypes.c_double]),
+        "mg_server_get_stats": (ctypes.c_int, [vp, ctypes.POINTER(MGServerStats)]),
+        "mg_server_destroy": (ctypes.c_int, [vp]),
         "mg_version": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():

@@ -1,4 +1,4 @@
-"""Serving loop: continuous batching of initial-conditions requests on one GPU.
+"""Serving loops: continuous batching of initial-conditions requests on one GPU.
 
 A request is one hierarchy's whole step (1LPT, 2LPT, both displacement fields)
 with its density delta in pinned host memory; the result comes back to pinned
@@ -12,9 +12,12 @@ as a worker slot is free and their hierarchy fits the HBM budget:
   request whose geometry was seen before reuses the resident levels and its
   captured CUDA graphs; when requests of one configuration overlap, the cache
   holds several instances of it (budget permitting) so they run concurrently;
-* overlap: every worker drives its own CUDA stream and the library call holds
-  no Python lock, so requests that arrive while others are on the GPU run
-  concurrently with them;
+* overlap: in Server every worker thread drives its own CUDA stream and the
+  library call holds no Python lock, so requests that arrive while others are on
+  the GPU run concurrently with them; in NativeServer (mg_server_*) one C++
+  scheduler thread drives all admitted requests as non-blocking pipelines, each
+  on its hierarchy's stream, advancing a request whenever the work it queued last
+  has finished;
 * each result depends only on its own request: the same kernels on the same
   data, no arithmetic shared between requests, so a result is bit-identical
   alone and in the mix.
@@ -210,6 +213,128 @@ class Server:
         for t in self.threads:
             t.join(timeout=60)
         self.admission.clear()
+
+
+def _monotonic_perf_counter():
+    info = time.get_clock_info("perf_counter")
+    return "CLOCK_MONOTONIC" in info.implementation and "RAW" not in info.implementation
+
+
+class NativeServer:
+    """The native serving runtime (mg_server_*): the same admission by HBM budget
+    and per-configuration cache of resident hierarchies as Server, but one C++
+    scheduler thread drives every admitted request as a non-blocking pipeline
+    (an event query per running request and loop pass) instead of one Python
+    thread per request blocking on its stream.  Up to `max_active` requests run
+    on the GPU at once.  Results are bit-identical to a solo
+    Hierarchy.pipeline(host=True) call."""
+
+    def __init__(self, max_active=16, hbm_budget=32 << 30, keep_outputs=True, workers=None):
+        import ctypes
+        import torch
+        self._ct = ctypes
+        self._torch = torch
+        self.keep_outputs = keep_outputs
+        self.hbm_budget = int(hbm_budget)
+        self.max_active = int(workers if workers is not None else max_active)
+        self.lib = mg.load_library()
+        handle = ctypes.c_void_p()
+        st = self.lib.mg_server_create(self.hbm_budget, self.max_active, ctypes.byref(handle))
+        if st != 0:
+            raise mg.MGError(st, "mg_server_create")
+        self.h = handle
+        self.lock = threading.Condition()
+        self.inflight = {}       # id -> (request, kept buffers)
+        self.completed = []
+        self.peak_inflight = 0
+        self._next_id = 0
+        self._stop = False
+        self._clock_ok = _monotonic_perf_counter()
+        self._poller = threading.Thread(target=self._poll_loop, daemon=True)
+        self._poller.start()
+
+    def submit(self, req):
+        ct = self._ct
+        if req.arrival is None:
+            req.arrival = time.perf_counter()
+        nbytes = mg.workspace_bytes(req.cfg)
+        if nbytes == 0:
+            raise mg.MGError(1, "invalid configuration: " + mg.validate(req.cfg)[1])
+        if nbytes > self.hbm_budget:
+            raise mg.MGError(2, "request needs %d bytes, above the HBM budget" % nbytes)
+        shapes = _leaf_shapes(req.cfg)
+        pin = lambda s: self._torch.empty(s, dtype=self._torch.float64, pin_memory=True)
+        out = {"phi1": [pin(s) for s in shapes], "phi2": [pin(s) for s in shapes],
+               "disp1": [pin(s) for s in shapes for _ in range(3)],
+               "disp2": [pin(s) for s in shapes for _ in range(3)]}
+        d3 = [s for s in shapes for _ in range(3)]
+        arrays = [mg._ptrs(req.deltas, shapes, True), mg._ptrs(out["phi1"], shapes, True),
+                  mg._ptrs(out["phi2"], shapes, True), mg._ptrs(out["disp1"], d3, True),
+                  mg._ptrs(out["disp2"], d3, True)]
+        cast = lambda a: ct.cast(a, ct.POINTER(ct.c_void_p))
+        with self.lock:
+            rid = self._next_id
+            self._next_id += 1
+            self.inflight[rid] = (req, out, arrays, req.cfg)
+            self.peak_inflight = max(self.peak_inflight, len(self.inflight))
+        st = self.lib.mg_server_submit(self.h, rid, ct.byref(req.cfg), *[cast(a) for a in arrays])
+        if st != 0:
+            with self.lock:
+                del self.inflight[rid]
+            raise mg.MGError(st, "mg_server_submit")
+
+    def _poll_loop(self):
+        buf = (mg.MGServerResult * 64)()
+        while True:
+            n = self.lib.mg_server_poll(self.h, buf, 64, 0.05)
+            if n <= 0:
+                if self._stop:
+                    return
+                continue
+            now = time.perf_counter()
+            with self.lock:
+                for i in range(n):
+                    r = buf[i]
+                    req, out, _, _ = self.inflight.pop(r.id)
+                    req.admitted = r.t_start if self._clock_ok else None
+                    req.done = r.t_done if self._clock_ok else now
+                    req.info = (r.info1.as_dict(), r.info2.as_dict())
+                    if r.status != 0:
+                        req.error = mg.MGError(r.status, "request %d: %s"
+                                               % (req.id, r.error.decode(errors="replace")))
+                    req.outputs = out if self.keep_outputs else None
+                    self.completed.append(req)
+                self.lock.notify_all()
+
+    def stats(self):
+        st = mg.MGServerStats()
+        self.lib.mg_server_get_stats(self.h, self._ct.byref(st))
+        return st.as_dict()
+
+    def drain(self, timeout=600.0):
+        """Wait until every submitted request has completed."""
+        end = time.perf_counter() + timeout
+        with self.lock:
+            while self.inflight and time.perf_counter() < end:
+                self.lock.wait(timeout=0.05)
+            return not self.inflight
+
+    def close(self):
+        """Stops the server: requests not yet started fail, running ones finish;
+        results not collected by then are dropped (drain() first to keep them)."""
+        if self.h is None:
+            return
+        self._stop = True
+        self._poller.join(timeout=60)
+        self.lib.mg_server_destroy(self.h)
+        self.h = None
+
+
+def _leaf_shapes(cfg):
+    shapes = [tuple(cfg.base_n)]
+    for i in range(cfg.n_levels - 1):
+        shapes.append(tuple(cfg.nest_n[i]))
+    return shapes
 
 
 def run_open_loop(server, requests, rate, seed=5):

@@ -152,3 +152,115 @@ def test_concurrent_creation_from_one_shared_config():
         for key in ("phi1", "phi2", "disp1", "disp2"):
             for a, b in zip(out[key], want[key]):
                 assert torch.equal(a, b), key
+
+
+def _native_setup():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1103_6031_gb300 as pkg
+    return torch, pkg
+
+
+@pytest.mark.gpu
+def test_native_server_results_equal_solo_runs_under_eviction():
+    """mg_server_*: mixed float64 and mixed-precision requests of three
+    configurations, several of each in flight at once, under a budget of about
+    two hierarchies (so idle ones are closed to make room); every result equals a
+    solo Hierarchy.pipeline(host=True) bit for bit."""
+    torch, pkg = _native_setup()
+    from paper_1103_6031_gb300.serve import NativeServer, Request, latency_stats, run_open_loop
+
+    def cfg(i):
+        g, mixed = GEOMS[i % len(GEOMS)]
+        kw = dict(tol=1e-9, max_cycles=40)
+        if mixed:
+            kw.update(precision=pkg.MG_MIXED, inner_cycles=3)
+        return pkg.config_from_geometry(g, **kw)
+
+    inputs = [[torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+               for x in make_delta(g, 70 + i)] for i, (g, _) in enumerate(GEOMS)]
+    n = 30
+    reqs = [Request(k, cfg(k), inputs[k % len(GEOMS)]) for k in range(n)]
+    budget = 2 * max(pkg.workspace_bytes(cfg(i)) for i in range(len(GEOMS)))
+    server = NativeServer(max_active=4, hbm_budget=budget)
+    run_open_loop(server, reqs, rate=3000.0)
+    st = server.stats()
+    server.close()
+    stats = latency_stats(reqs)
+    assert stats["count"] == n and stats["p99_ms"] >= stats["p50_ms"] > 0
+    assert st["completed"] == n and st["pending"] == 0 and st["active"] == 0
+    assert st["evictions"] > 0 and st["peak_bytes"] <= budget and st["peak_active"] >= 2
+    for k in range(len(GEOMS)):
+        alone = pkg.Hierarchy(cfg(k))
+        out, i1, i2 = alone.pipeline(inputs[k], host=True)
+        alone.close()
+        for r in reqs[k::len(GEOMS)]:
+            assert r.error is None, r.error
+            assert r.info[0]["cycles"] == i1["cycles"] and r.info[1]["cycles"] == i2["cycles"]
+            assert r.admitted is None or r.arrival <= r.admitted + 1e-3
+            for key in ("phi1", "phi2", "disp1", "disp2"):
+                for a, b in zip(r.outputs[key], out[key]):
+                    assert torch.equal(a, b), (r.id, key)
+
+
+@pytest.mark.gpu
+def test_native_server_runs_overlapping_requests_of_one_config_concurrently():
+    """Eight requests of one configuration at once get one hierarchy each (the
+    budget holds them all) and run together."""
+    torch, pkg = _native_setup()
+    from paper_1103_6031_gb300.serve import NativeServer, Request
+    geom = small_zoom(24, ((20, 7),), order=6, box=50.0)
+    cfg = pkg.config_from_geometry(geom, tol=1e-9, max_cycles=40)
+    deltas = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in make_delta(geom, 91)]
+    server = NativeServer(max_active=8, hbm_budget=64 * pkg.workspace_bytes(cfg))
+    reqs = [Request(k, cfg, deltas) for k in range(8)]
+    for r in reqs:
+        server.submit(r)
+    assert server.drain(timeout=120)
+    st = server.stats()
+    server.close()
+    assert st["instances"] == st["created"] >= 2 and st["evictions"] == 0
+    first = reqs[0].outputs
+    for r in reqs:
+        assert r.error is None, r.error
+        for key in ("phi1", "phi2", "disp1", "disp2"):
+            for a, b in zip(r.outputs[key], first[key]):
+                assert torch.equal(a, b), key
+
+
+@pytest.mark.gpu
+def test_native_server_rejects_invalid_and_oversized_requests():
+    torch, pkg = _native_setup()
+    from paper_1103_6031_gb300 import mg
+    from paper_1103_6031_gb300.serve import NativeServer, Request
+    geom = Geometry((32, 32, 32), 64.0, 2, ())
+    good = pkg.config_from_geometry(geom, tol=1e-9, max_cycles=40)
+    deltas = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in make_delta(geom, 5)]
+    server = NativeServer(max_active=2, hbm_budget=pkg.workspace_bytes(good))
+    bad = pkg.config_from_geometry(geom, tol=1e-9, max_cycles=40)
+    bad.order = 5
+    with pytest.raises(mg.MGError) as e1:
+        server.submit(Request(0, bad, deltas))
+    assert e1.value.status == 1
+    big_geom = Geometry((64, 64, 64), 64.0, 2, ())
+    big = pkg.config_from_geometry(big_geom, tol=1e-9, max_cycles=40)
+    with pytest.raises(mg.MGError) as e2:
+        server.submit(Request(1, big, deltas))
+    assert e2.value.status == 2
+    # the C entry point checks the same on its own
+    import ctypes
+    arr = ctypes.cast(mg._ptrs(deltas, [(32, 32, 32)], True), ctypes.POINTER(ctypes.c_void_p))
+    assert server.lib.mg_server_submit(server.h, 98, ctypes.byref(bad), arr, None, None, None,
+                                       None) == 1
+    assert server.lib.mg_server_submit(server.h, 99, ctypes.byref(big), arr, None, None, None,
+                                       None) == 2
+    assert server.lib.mg_server_submit(server.h, 97, ctypes.byref(good), None, None, None, None,
+                                       None) == 1
+    r = Request(2, good, deltas)
+    server.submit(r)
+    assert server.drain(timeout=60)
+    server.close()
+    assert r.error is None and r.info[0]["rel_residual"] <= 1e-9

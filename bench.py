@@ -56,6 +56,13 @@ SMOOTH_BYTES_PER_CELL = 16.0
 # capture of the 128^3 launch; scaled per launch by
 # the updated cells.  Set to None whenever the kernel changes.
 SMOOTH_TRAFFIC_PER_UPDATE = 35.8
+# the same for k_smooth_half<6,float> (ncu capture of the 128^3 nest launch) and for
+# k_smooth_half_tma<6,float> (capture of the 256^3 nest launch)
+SMOOTH_F32_TRAFFIC_PER_UPDATE = 17.8
+SMOOTH_TMA_F32_TRAFFIC_PER_UPDATE = 22.3
+# float32 levels of at least this many cells that are not periodic take the
+# TMA-staged smoother by default
+TMA_MIN_CELLS = 1 << 23
 
 
 # Workloads: zoom2 is the headline; the others are the single-level and deep-zoom
@@ -720,6 +727,22 @@ def run_ours(args):
         # float32 in place: 8 B per level-cell (read u of both colours 4 B, f of the
         # updated colour 2 B, write the updated colour 2 B)
         m_gbs = 8.0 * 2 * m_upd / (m_ms * 1e-3) / 1e9
+        # which kernel the timed launches ran: the plain one on the periodic base and
+        # on smaller nests, the TMA-staged one on float32 nests of >= 2^23 cells
+        shapes = level_shapes(geom)
+        tma_nests = [n for n in shapes[1:] if n[0] * n[1] * n[2] // 2 == dominant
+                     and n[0] * n[1] * n[2] >= TMA_MIN_CELLS]
+        base_big = shapes[0][0] * shapes[0][1] * shapes[0][2] // 2 == dominant
+        if not tma_nests:
+            m_kernel = "k_smooth_half<%d,float> (%s levels)" % (geom.order, big)
+            m_traffic = SMOOTH_F32_TRAFFIC_PER_UPDATE * m_upd if geom.order == 6 else None
+        elif not base_big:
+            m_kernel = "k_smooth_half_tma<%d,float> (%s nests)" % (geom.order, big)
+            m_traffic = SMOOTH_TMA_F32_TRAFFIC_PER_UPDATE * m_upd if geom.order == 6 else None
+        else:
+            m_kernel = ("k_smooth_half<%d,float> (%s periodic base) and k_smooth_half_tma<%d,"
+                        "float> (%s nests)" % (geom.order, big, geom.order, big))
+            m_traffic = None
         mixed = {"value": mixed_value, "unit": UNIT, "ms_per_step": mixed_ms_step,
                  "latency_ms": {"p50": statistics.median(mixed_ms),
                                 "p99": sorted(mixed_ms)[max(0, int(round(0.99 * len(mixed_ms))) - 1)]},
@@ -731,8 +754,9 @@ def run_ours(args):
                                   "2lpt": m2["rel_residual"] if m2 else None},
                  "gpu_launches": sum(v["launches"] for v in mstats.values()),
                  "roofline": {"bound": "hbm", "achieved": m_gbs, "peak": HBM_PEAK_GBS,
-                              "unit": "GB/s", "frac": m_gbs / HBM_PEAK_GBS, "traffic": None,
-                              "kernel": "k_smooth_half<%d,float> (%s levels)" % (geom.order, big),
+                              "unit": "GB/s", "frac": m_gbs / HBM_PEAK_GBS, "traffic": m_traffic,
+                              "traffic_unit": "bytes per launch (ncu, scaled by updated cells)",
+                              "kernel": m_kernel,
                               "peak_source": "measured copy bandwidth (of measured)",
                               "ms_per_launch": m_ms, "updates_per_launch": m_upd,
                               "bytes_per_cell": 8.0},

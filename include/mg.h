@@ -84,6 +84,12 @@ typedef enum { MG_FP64 = 0, MG_MIXED = 1 } mg_precision;
  * the hybrid Poisson solver correction on the finest level (Sec. 3.5.2, see
  * mg_hybrid_correction) with that level's source (delta for psi1, tau for psi2). */
 #define MG_FLAG_HYBRID 8
+/* MG_FLAG_DEVICE_LOOP: the iteration loop of every solve runs on the device: one
+ * CUDA graph per solve whose while node repeats the iteration and whose last
+ * kernel applies the stopping rule (and, in MG_MIXED, the inner-cycle plan) of the
+ * host loop, so no host round trip separates two iterations.  Same launches and
+ * results as the host loop; ignored with MG_FLAG_NO_GRAPHS or while profiling. */
+#define MG_FLAG_DEVICE_LOOP 16
 
 typedef struct {
   int n_levels;                        /* 1 = base only; 1 + number of nests            */

@@ -119,6 +119,103 @@ struct Graph {
 
 }  // namespace
 
+// Kernels of the device-side iteration loop live in a named namespace (kernels in
+// this file's anonymous namespace would clash with those of mgk's).
+namespace mgloop {
+
+// Convergence record of a solve whose iteration loop runs on the device
+// (MG_FLAG_DEVICE_LOOP), written by k_loop_step after every iteration.
+struct LoopState {
+  int c;            // iterations run
+  int done;
+  int timeout;      // a smoother block's bounded wait ran out
+  int at_floor;     // residual at the rounding level of the source
+  int inner_now;    // MG_MIXED: float32 V-cycles of the next outer iteration
+  int inner_total;  // MG_MIXED: float32 V-cycles run
+  double rel;       // relative leaf residual after the last iteration
+  double source_mean;
+  double history[MG_MAX_HISTORY];
+  unsigned char inner_hist[MG_MAX_HISTORY];  // MG_MIXED: inner cycles per iteration
+};
+
+__host__ __device__ inline int inner_plan(int cap, double tol, double rel_before, double rel_after,
+                                          int used) {
+  if (!(tol > 0.0) || !(rel_after > 0.0) || !(rel_before > rel_after) || used < 1) return cap;
+  const double c = log(5.0);
+  const double k = (log(rel_before / rel_after) + c) / used;
+  const double need = (log(rel_after / (0.25 * tol)) + c) / k;
+  if (!(need == need) || need > 1e9 || need < -1e9) return cap;
+  const int n = (int)ceil(need);
+  return n < 1 ? 1 : (n > cap ? cap : n);
+}
+
+struct LoopParams {
+  double tol;
+  double volume;
+  int max_cycles;
+  int mixed;
+  int cap;
+};
+
+__global__ void k_loop_init(LoopState* st, int mixed, int cap) {
+  st->c = 0;
+  st->done = 0;
+  st->timeout = 0;
+  st->at_floor = 0;
+  st->inner_now = cap;
+  st->inner_total = 0;
+  // MG_MIXED starts from u = 0, whose residual is the source itself
+  st->rel = mixed ? 1.0 : INFINITY;
+  st->source_mean = 0.0;
+}
+
+// After iteration st->c: the same record and stopping rule as solve_step_read.
+__global__ void k_loop_step(LoopState* st, const double* red, LoopParams p,
+                            cudaGraphConditionalHandle while_h, cudaGraphConditionalHandle switch_h) {
+  const double rr = red[0], ff = red[1], fs = red[2];
+  const unsigned flag = *reinterpret_cast<const unsigned*>(red + 4);
+  const int c = st->c;
+  if (c == 0) st->source_mean = fs / p.volume;
+  const double before = st->rel;
+  const double rel = ff > 0.0 ? sqrt(rr) / sqrt(ff) : sqrt(rr);
+  st->rel = rel;
+  if (p.mixed) {
+    st->inner_total += st->inner_now;
+    if (c < MG_MAX_HISTORY) st->inner_hist[c] = (unsigned char)st->inner_now;
+    st->inner_now = inner_plan(p.cap, p.tol, before, rel, st->inner_now);
+  }
+  if (c < MG_MAX_HISTORY) st->history[c] = rel;
+  st->c = c + 1;
+  const bool fixed = !(p.tol > 0.0);
+  const double mean = st->source_mean;
+  const double floor_ = 64.0 * DBL_EPSILON * sqrt(ff + p.volume * mean * mean);
+  const bool at_floor = !fixed && sqrt(rr) <= floor_;
+  const bool finite = rel == rel && rel < INFINITY;
+  const bool done = !finite || (!fixed && rel <= p.tol) || at_floor || c + 1 >= p.max_cycles ||
+                    flag != 0;
+  st->at_floor = at_floor ? 1 : 0;
+  st->timeout = flag != 0 ? 1 : 0;
+  st->done = done ? 1 : 0;
+  cudaGraphSetConditional(while_h, done ? 0u : 1u);
+  if (p.mixed) cudaGraphSetConditional(switch_h, (unsigned)(st->inner_now - 1));
+}
+
+}  // namespace mgloop
+
+using mgloop::LoopState;
+
+namespace {
+
+struct LoopGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  mg_stats body[17];  // launches of one iteration: [0] FP64 V-cycle + norm;
+                      // MG_MIXED: [n] zero correction + n float32 V-cycles
+  mg_stats tail;      // MG_MIXED: update, ghosts and norm after the inner cycles
+};
+
+}  // namespace
+
 struct mg_hierarchy {
   mg_config cfg;
   std::vector<DevLevel> L;
@@ -150,6 +247,10 @@ struct mg_hierarchy {
   HybridFFT* hybrid = nullptr;
   double* hybrid_f = nullptr;  // dense source of the finest level
   double volume = 0.0;
+  // device-side iteration loop (MG_FLAG_DEVICE_LOOP), built on first use
+  LoopGraph loop;
+  LoopState* loop_dev = nullptr;
+  LoopState* loop_host = nullptr;  // pinned copy written at the end of the loop graph
   // launch counters and optional CUDA-event timing per kernel family
   mg_stats stats;
   unsigned prof_mask = 0;    // families the caller asked to time
@@ -568,7 +669,7 @@ mg_status sync_covered(mg_hierarchy* h) {
 // host synchronisation, so it can be captured); ends with the copy of 4
 // doubles to pinned host memory.  In MG_MIXED the residual is also stored
 // (float32) as the correction source.
-mg_status norm_launches(mg_hierarchy* h, bool zero_u = false) {
+mg_status norm_launches(mg_hierarchy* h, bool zero_u = false, bool copy_out = true) {
   if (!zero_u) ST(sync_covered(h));
   for (int l = h->base; l <= finest(h); ++l) {
     DevLevel& L = h->L[l];
@@ -582,7 +683,8 @@ mg_status norm_launches(mg_hierarchy* h, bool zero_u = false) {
   }
   KL(MG_K_NORM, h->partial_slots,
      launch_reduce_partials(h->partial, h->partial_slots, 2, h->red, h->s));
-  CK(cudaMemcpyAsync(h->host_red, h->red, 5 * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+  if (copy_out)
+    CK(cudaMemcpyAsync(h->host_red, h->red, 5 * sizeof(double), cudaMemcpyDeviceToHost, h->s));
   return MG_OK;
 }
 
@@ -793,15 +895,7 @@ mg_status solve_begin_read(mg_hierarchy* h, SolveState& st) {
 // single cycles that left the residual where it was (deep nests: 1.3e-7 -> 1.7e-7),
 // costing a whole further outer iteration.
 int next_inner_cycles(const mg_hierarchy* h, double rel_before, double rel_after, int used) {
-  const int cap = h->cfg.inner_cycles;
-  if (!(h->cfg.tol > 0.0) || !(rel_after > 0.0) || !(rel_before > rel_after) || used < 1)
-    return cap;
-  const double c = std::log(5.0);
-  const double k = (std::log(rel_before / rel_after) + c) / used;
-  const double need = (std::log(rel_after / (0.25 * h->cfg.tol)) + c) / k;
-  if (!std::isfinite(need)) return cap;
-  const int n = (int)std::ceil(need);
-  return n < 1 ? 1 : (n > cap ? cap : n);
+  return mgloop::inner_plan(h->cfg.inner_cycles, h->cfg.tol, rel_before, rel_after, used);
 }
 
 // The launches of one V-cycle (MG_FP64) or one outer iteration (MG_MIXED).
@@ -866,10 +960,184 @@ mg_status solve_end(mg_hierarchy* h, SolveState& st, mg_info* info) {
   return res;
 }
 
+// ---- device-side iteration loop (MG_FLAG_DEVICE_LOOP) ----------------------------
+//
+// The whole iteration loop of a solve as one CUDA graph: a while node repeats the
+// iteration (MG_FP64: V-cycle + norm; MG_MIXED: a switch node selecting the body
+// with the planned number of float32 V-cycles, then the float64 update and norm)
+// followed by k_loop_step, which applies the stopping rule and the inner-cycle plan
+// of the host loop on the device and sets the conditions for the next pass.  The
+// host launches the graph once per solve and reads the record at the end, so no
+// host round trip separates two iterations.
+
+bool device_loop_on(const mg_hierarchy* h) {
+  return (h->cfg.flags & MG_FLAG_DEVICE_LOOP) && !(h->cfg.flags & MG_FLAG_NO_GRAPHS) &&
+         h->prof_mask == 0 && h->cfg.max_cycles >= 1 && h->cfg.inner_cycles <= 16;
+}
+
+// Captures body(h) on the hierarchy's stream into graph g (after the nodes in
+// deps); the launches are counted into *delta instead of the statistics.
+template <typename Body>
+mg_status capture_into(mg_hierarchy* h, cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps,
+                       mg_stats* delta, Body body) {
+  const mg_stats snap = h->stats;
+  CK(cudaStreamBeginCaptureToGraph(h->s, g, deps, nullptr, ndeps, cudaStreamCaptureModeRelaxed));
+  const unsigned keep = h->active_mask;
+  h->active_mask = 0;
+  const mg_status st = body(h);
+  h->active_mask = keep;
+  cudaGraph_t out = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(h->s, &out);
+  for (int f = 0; f < MG_K_FAMILIES; ++f) {
+    delta->launches[f] = h->stats.launches[f] - snap.launches[f];
+    delta->cells[f] = h->stats.cells[f] - snap.cells[f];
+  }
+  h->stats = snap;
+  ST(st);
+  CK(e);
+  return MG_OK;
+}
+
+mg_status build_loop_graph(mg_hierarchy* h) {
+  LoopGraph& G = h->loop;
+  if (!h->loop_dev) CK(cudaMalloc(&h->loop_dev, sizeof(LoopState)));
+  if (!h->loop_host) CK(cudaHostAlloc(&h->loop_host, sizeof(LoopState), cudaHostAllocDefault));
+  CK(cudaGraphCreate(&G.graph, 0));
+  cudaGraph_t g = G.graph;
+  const int cap = h->mixed ? h->cfg.inner_cycles : 0;
+  cudaGraphConditionalHandle while_h = 0, switch_h = 0;
+  CK(cudaGraphConditionalHandleCreate(&while_h, g, 1u, cudaGraphCondAssignDefault));
+  if (h->mixed)
+    CK(cudaGraphConditionalHandleCreate(&switch_h, g, (unsigned)(cap - 1), cudaGraphCondAssignDefault));
+  // record initialisation
+  mg_stats none;
+  LoopState* dev = h->loop_dev;
+  const int mixed = h->mixed ? 1 : 0;
+  ST(capture_into(h, g, nullptr, 0, &none, [&](mg_hierarchy* hh) -> mg_status {
+    mgloop::k_loop_init<<<1, 1, 0, hh->s>>>(dev, mixed, cap);
+    return cudaGetLastError() == cudaSuccess ? MG_OK : fail(hh, MG_ECUDA, "k_loop_init launch");
+  }));
+  cudaGraphNode_t init = nullptr;
+  size_t n = 1;
+  CK(cudaGraphGetNodes(g, &init, &n));
+  // the loop
+  cudaGraphNodeParams wp = {};
+  std::memset(&wp, 0, sizeof(wp));
+  wp.type = cudaGraphNodeTypeConditional;
+  wp.conditional.handle = while_h;
+  wp.conditional.type = cudaGraphCondTypeWhile;
+  wp.conditional.size = 1;
+  cudaGraphNode_t loop = nullptr;
+  CK(cudaGraphAddNode(&loop, g, &init, nullptr, 1, &wp));
+  cudaGraph_t body = wp.conditional.phGraph_out[0];
+  mgloop::LoopParams lp;
+  lp.tol = h->cfg.tol;
+  lp.volume = h->volume;
+  lp.max_cycles = h->cfg.max_cycles;
+  lp.mixed = mixed;
+  lp.cap = cap;
+  const double* red = h->red;
+  auto step = [&](mg_hierarchy* hh) -> mg_status {
+    mgloop::k_loop_step<<<1, 1, 0, hh->s>>>(dev, red, lp, while_h, switch_h);
+    return cudaGetLastError() == cudaSuccess ? MG_OK : fail(hh, MG_ECUDA, "k_loop_step launch");
+  };
+  if (!h->mixed) {
+    ST(capture_into(h, body, nullptr, 0, &G.body[0], [&](mg_hierarchy* hh) -> mg_status {
+      ST(vcycle<double>(hh, finest(hh)));
+      ST(norm_launches(hh, false, false));
+      return step(hh);
+    }));
+  } else {
+    cudaGraphNodeParams sp = {};
+    std::memset(&sp, 0, sizeof(sp));
+    sp.type = cudaGraphNodeTypeConditional;
+    sp.conditional.handle = switch_h;
+    sp.conditional.type = cudaGraphCondTypeSwitch;
+    sp.conditional.size = (unsigned)cap;
+    cudaGraphNode_t sw = nullptr;
+    CK(cudaGraphAddNode(&sw, body, nullptr, nullptr, 0, &sp));
+    for (int m = 1; m <= cap; ++m) {
+      ST(capture_into(h, sp.conditional.phGraph_out[m - 1], nullptr, 0, &G.body[m],
+                      [&](mg_hierarchy* hh) -> mg_status {
+                        ST(zero_correction(hh));
+                        for (int k = 0; k < m; ++k) ST(vcycle<float>(hh, finest(hh)));
+                        return MG_OK;
+                      }));
+    }
+    ST(capture_into(h, body, &sw, 1, &G.tail, [&](mg_hierarchy* hh) -> mg_status {
+      for (int l = hh->base; l <= finest(hh); ++l) {
+        DevLevel& L = hh->L[l];
+        KL(MG_K_PROLONG, cells_of(L.G),
+           launch_add_correction(L.G, phi_of(L), L.s.u[L.s.cur], L.periodic ? 1 : 0, hh->s));
+      }
+      for (int l = hh->base + 1; l <= finest(hh); ++l) ST(tangential<double>(hh, l));
+      ST(norm_launches(hh, false, false));
+      return step(hh);
+    }));
+  }
+  cudaGraphNode_t copy = nullptr;
+  CK(cudaGraphAddMemcpyNode1D(&copy, g, &loop, 1, h->loop_host, h->loop_dev, sizeof(LoopState),
+                              cudaMemcpyDeviceToHost));
+  CK(cudaGraphInstantiate(&G.exec, g, 0));
+  return MG_OK;
+}
+
+mg_status ensure_loop_graph(mg_hierarchy* h) {
+  if (h->loop.exec) return MG_OK;
+  const mg_status st = build_loop_graph(h);
+  if (st != MG_OK) {
+    if (h->loop.graph) cudaGraphDestroy(h->loop.graph);
+    h->loop = LoopGraph();
+  }
+  return st;
+}
+
+// Launches the loop graph (after solve_begin); the record is read by loop_read.
+mg_status loop_launch(mg_hierarchy* h) {
+  ST(ensure_loop_graph(h));
+  CK(cudaGraphLaunch(h->loop.exec, h->s));
+  return MG_OK;
+}
+
+// The loop graph has finished: its record into st (as the host loop leaves it) and
+// its launches into the statistics.
+mg_status loop_read(mg_hierarchy* h, SolveState& st) {
+  const LoopState& R = *h->loop_host;
+  std::memset(&st.local, 0, sizeof(st.local));
+  st.local.cycles = R.c;
+  for (int i = 0; i < R.c && i < MG_MAX_HISTORY; ++i) st.local.history[i] = R.history[i];
+  st.local.source_mean = R.source_mean;
+  st.local.inner_cycles = R.inner_total;
+  st.rel = R.rel;
+  st.at_floor = R.at_floor != 0;
+  st.c = R.c;
+  st.done = true;
+  for (int i = 0; i < R.c; ++i) {
+    const mg_stats& d = h->mixed ? h->loop.body[i < MG_MAX_HISTORY ? R.inner_hist[i]
+                                                                   : h->cfg.inner_cycles]
+                                 : h->loop.body[0];
+    for (int f = 0; f < MG_K_FAMILIES; ++f) {
+      h->stats.launches[f] += d.launches[f] + (h->mixed ? h->loop.tail.launches[f] : 0);
+      h->stats.cells[f] += d.cells[f] + (h->mixed ? h->loop.tail.cells[f] : 0);
+    }
+  }
+  if (h->mixed) h->inner_now = R.inner_now;
+  if (R.timeout)
+    return fail(h, MG_ETIMEOUT,
+                "a smoother block's wait for a staged plane tile ran out; outputs are invalid");
+  return MG_OK;
+}
+
 mg_status solve_prepared(mg_hierarchy* h, mg_info* info) {
   SolveState st;
   ST(solve_begin(h));
   ST(solve_begin_read(h, st));
+  if (device_loop_on(h)) {
+    ST(loop_launch(h));
+    CK(cudaStreamSynchronize(h->s));
+    ST(loop_read(h, st));
+    return solve_end(h, st, info);
+  }
   while (!st.done) {
     ST(run_body(h, st.c == 0, solve_body));
     ST(solve_step_read(h, st));
@@ -1255,7 +1523,10 @@ mg_status job_begin_solve(PipelineJob* j) {
   mg_hierarchy* h = j->h;
   ST(solve_begin(h));
   ST(solve_begin_read(h, j->st));
-  ST(run_body(h, true, solve_body));
+  if (device_loop_on(h))
+    ST(loop_launch(h));
+  else
+    ST(run_body(h, true, solve_body));
   return job_record(j);
 }
 
@@ -1272,10 +1543,14 @@ mg_status job_store(PipelineJob* j, const std::vector<double*>& phi,
 // The iteration queued last has finished: read it and queue what comes next.
 mg_status job_advance(PipelineJob* j) {
   mg_hierarchy* h = j->h;
-  ST(solve_step_read(h, j->st));  // its stream synchronisation returns at once
-  if (!j->st.done) {
-    ST(run_body(h, false, solve_body));
-    return job_record(j);
+  if (device_loop_on(h)) {
+    ST(loop_read(h, j->st));  // the whole loop of the solve has run
+  } else {
+    ST(solve_step_read(h, j->st));  // its stream synchronisation returns at once
+    if (!j->st.done) {
+      ST(run_body(h, false, solve_body));
+      return job_record(j);
+    }
   }
   const int k = j->phase - 1;
   const mg_status e = solve_end(h, j->st, &j->info[k]);
@@ -1666,6 +1941,10 @@ mg_status mg_hierarchy_destroy(mg_hierarchy* h) {
     else cudaFree(h->arena);
   }
   if (h->host_red) cudaFreeHost(h->host_red);
+  if (h->loop.exec) cudaGraphExecDestroy(h->loop.exec);
+  if (h->loop.graph) cudaGraphDestroy(h->loop.graph);
+  cudaFree(h->loop_dev);
+  if (h->loop_host) cudaFreeHost(h->loop_host);
   hybrid_destroy(h->hybrid);
   cudaFree(h->hybrid_f);
   for (int f = 0; f < MG_K_FAMILIES; ++f) {

@@ -1394,9 +1394,37 @@ mg_status batch_graph(mg_batch* b, const std::vector<int>& active, BatchGraph** 
   return MG_OK;
 }
 
+// Members with the device-side loop: each member's loop graph on its own stream,
+// all launched before the first wait, so the members run concurrently and each one
+// stops on its own.
+mg_status batch_solve_device_loops(mg_batch* b, mg_info* infos) {
+  const size_t n = b->m.size();
+  std::vector<SolveState> st(n);
+  for (size_t i = 0; i < n; ++i) {
+    mg_hierarchy* h = b->m[i];
+    mg_status r = solve_begin(h);
+    if (r == MG_OK) r = solve_begin_read(h, st[i]);
+    if (r == MG_OK) r = loop_launch(h);
+    if (r != MG_OK) return member_status(b, (int)i, r);
+  }
+  mg_status worst = MG_OK;
+  for (size_t i = 0; i < n; ++i) {
+    mg_hierarchy* h = b->m[i];
+    BCK(cudaStreamSynchronize(h->s));
+    mg_status r = loop_read(h, st[i]);
+    if (r == MG_OK || r == MG_ENOCONV) r = solve_end(h, st[i], infos ? &infos[i] : nullptr);
+    if (r != MG_OK && r != MG_ENOCONV) return member_status(b, (int)i, r);
+    if (r == MG_ENOCONV) worst = MG_ENOCONV;
+  }
+  return worst;
+}
+
 // Solves every member; f of every member holds its source.
 mg_status batch_solve(mg_batch* b, mg_info* infos) {
   const size_t n = b->m.size();
+  bool loops = true;
+  for (size_t i = 0; i < n; ++i) loops = loops && device_loop_on(b->m[i]);
+  if (loops) return batch_solve_device_loops(b, infos);
   std::vector<SolveState> st(n);
   for (size_t i = 0; i < n; ++i) {
     mg_status r = solve_begin(b->m[i]);

@@ -120,3 +120,27 @@ def test_device_loop_through_native_server(lib):
         for key in ("phi1", "phi2", "disp1", "disp2"):
             for a, b in zip(r.outputs[key], want[key]):
                 assert torch.equal(a, b), key
+
+
+def test_device_loops_in_a_batch_equal_solo_host_loops(lib):
+    """A batch whose members all run device-side loops launches every member's loop
+    graph on its own stream; each member's results equal its solo host-loop run."""
+    import torch
+    members = [(geom, mixed, _inputs(geom, 20 + i)) for i, (_, geom, mixed) in enumerate(CASES)]
+    want = []
+    for geom, mixed, d in members:
+        h = lib.Hierarchy(_cfg(lib, geom, mixed, False))
+        want.append(h.pipeline(d))
+        h.close()
+    hs = [lib.Hierarchy(_cfg(lib, geom, mixed, True)) for geom, mixed, _ in members]
+    batch = lib.Batch(hs)
+    outs, i1, i2 = batch.pipeline([d for _, _, d in members])
+    batch.close()
+    for h in hs:
+        h.close()
+    for k, (wout, w1, w2) in enumerate(want):
+        _same_info(i1[k], w1)
+        _same_info(i2[k], w2)
+        for key in ("phi1", "phi2", "disp1", "disp2"):
+            for a, b in zip(outs[k][key], wout[key]):
+                assert torch.equal(a, b), (k, key)

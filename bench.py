@@ -371,18 +371,22 @@ def serving_measure(pkg, geoms, deltas_np, large, seconds, rate, workers, native
     kw = dict(tol=SOLVE_TOL, max_cycles=50, precision=pkg.MG_MIXED, inner_cycles=MIXED_INNER_CYCLES)
     cfg_small = [pkg.config_from_geometry(g, **kw) for g in geoms]
     cfg_large = pkg.config_from_geometry(large[0], **kw)
+    def draw(count, rng, first_id=0):
+        out, cells = [], 0
+        for k in range(count):
+            if rng.uniform() < 0.1:
+                out.append(serve.Request(first_id + k, cfg_large, large_in))
+                out[-1].cls = "large"
+                cells += large[0].level_cells()
+            else:
+                i = int(rng.integers(len(geoms)))
+                out.append(serve.Request(first_id + k, cfg_small[i], pinned[i]))
+                out[-1].cls = "batch_draw"
+                cells += geoms[i].level_cells()
+        return out, cells
+
     n = int(seconds * rate)
-    reqs, cells = [], 0
-    for k in range(n):
-        if rng.uniform() < 0.1:
-            reqs.append(serve.Request(k, cfg_large, large_in))
-            reqs[-1].cls = "large"
-            cells += large[0].level_cells()
-        else:
-            i = int(rng.integers(len(geoms)))
-            reqs.append(serve.Request(k, cfg_small[i], pinned[i]))
-            reqs[-1].cls = "batch_draw"
-            cells += geoms[i].level_cells()
+    reqs, cells = draw(n, rng)
     if native:
         server = serve.NativeServer(max_active=workers, hbm_budget=64 << 30, keep_outputs=False)
     else:
@@ -396,6 +400,11 @@ def serving_measure(pkg, geoms, deltas_np, large, seconds, rate, workers, native
     for r in warm:
         server.submit(r)
     server.drain()
+    # then one untimed second of the same arrival process (other seed): the steady
+    # state has the pinned output buffers cached and the busiest configurations with
+    # a second resident hierarchy
+    pre, _ = draw(int(rate), np.random.Generator(np.random.PCG64(SERVE_SEED + 1)), n)
+    serve.run_open_loop(server, pre, rate, seed=SERVE_SEED + 1)
     warm_s = time.perf_counter() - t0
     server.completed.clear()
     wall = serve.run_open_loop(server, reqs, rate, seed=SERVE_SEED)
@@ -420,8 +429,9 @@ def serving_measure(pkg, geoms, deltas_np, large, seconds, rate, workers, native
            "server": ("native: one C++ scheduler thread, non-blocking pipelines (mg_server_*)"
                       if native else "python: one thread per request in flight"),
            "workers": workers, "peak_inflight": server.peak_inflight,
-           "warmup": {"requests": len(warm), "seconds": warm_s,
-                      "what": "one untimed request per configuration before the timed window"},
+           "warmup": {"requests": len(warm) + len(pre), "seconds": warm_s,
+                      "what": "one untimed request per configuration, then one untimed second "
+                              "of the same arrival process, before the timed window"},
            "peak_resident_gb": peak_gb, "evictions": evictions, "errors": len(errors),
            "mix": "90%% draws from the 64 batched hierarchies, 10%% %d^3 base + 3 nests of %d^3 "
                   "(%.1f M level-cells); mixed precision; pinned host buffers in and out; "

@@ -65,6 +65,7 @@ struct DevLevel {
   FaceSet fs;
   int nblocks = 0;
   int partial_off = 0;
+  long long stage_off = 0;  // leaf levels: offset of the level's 4 dense arrays in stage
 };
 
 template <typename T>
@@ -243,6 +244,13 @@ struct mg_hierarchy {
   double* scratch = nullptr;   // 3 dense arrays of the largest leaf level
   long long scratch_elems = 0;
   double* tau_work = nullptr;  // 3 padded float64 arrays of the largest leaf level
+  // host-buffer pipelines: the first solve's phi and displacements are staged here
+  // (phi, x, y, z per leaf level, dense) and copied to the host on cs while the
+  // second solve runs
+  double* stage = nullptr;
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev_staged = nullptr, ev_copied = nullptr;
+  bool copies_pending = false;
   // hybrid Poisson correction of the finest level (MG_FLAG_HYBRID), made on first use
   HybridFFT* hybrid = nullptr;
   double* hybrid_f = nullptr;  // dense source of the finest level
@@ -356,6 +364,7 @@ size_t carve(const mg_config* cfg, const Plan& p, mg_hierarchy* h, char* arena) 
   const int g = cfg->order / 2;
   const bool mixed = cfg->precision == MG_MIXED;
   int slots = 0;
+  long long leaf_total = 0;
   long long max_leaf = 0;
   long long max_leaf_padded = 0;
   const size_t nl = p.geo.size();
@@ -419,6 +428,8 @@ size_t carve(const mg_config* cfg, const Plan& p, mg_hierarchy* h, char* arena) 
       }
       slots += norm_blocks(G);
       const long long dense = (long long)lg.n[0] * lg.n[1] * lg.n[2];
+      if (L) L->stage_off = 4 * leaf_total;
+      leaf_total += dense;
       if (dense > max_leaf) max_leaf = dense;
       if ((long long)e > max_leaf_padded) max_leaf_padded = (long long)e;
     }
@@ -431,8 +442,10 @@ size_t carve(const mg_config* cfg, const Plan& p, mg_hierarchy* h, char* arena) 
   double* red = c.take<double>(8);
   double* scratch = c.take<double>((size_t)3 * max_leaf);
   double* tau_work = c.take<double>((size_t)3 * max_leaf_padded);
+  double* stage = c.take<double>((size_t)4 * leaf_total);
   if (h) {
     h->tau_work = tau_work;
+    h->stage = stage;
     h->partial_slots = slots;
     h->partial = partial;
     h->red = red;
@@ -1274,6 +1287,54 @@ mg_status gradient_out(mg_hierarchy* h, double* const disp[], bool host, bool hy
   return MG_OK;
 }
 
+// Host-buffer pipelines: phi and the displacements of the solve just finished go
+// into the stage (dense, on the device) and their copies to the caller's host
+// buffers are queued on the copy stream, where they run while the work stream goes
+// on with tau and the second solve (the host link, ~190 GB/s, would otherwise add
+// the copies to the step).
+mg_status stage_outputs(mg_hierarchy* h, double* const phi[], double* const disp[]) {
+  if (!phi && !disp) return MG_OK;
+  std::vector<double*> dd;
+  for (int l = h->base; l <= finest(h); ++l) {
+    DevLevel& L = h->L[l];
+    const long long n = cells_of(L.G);
+    double* base = h->stage + L.stage_off;
+    if (phi && phi[l - h->base]) ST(store_leaf(h, l, phi_of(L), base, false));
+    for (int a = 1; a <= 3; ++a) dd.push_back(base + a * n);
+  }
+  if (disp) ST(gradient_out(h, dd.data(), false, true));
+  CK(cudaEventRecord(h->ev_staged, h->s));
+  CK(cudaStreamWaitEvent(h->cs, h->ev_staged, 0));
+  h->copies_pending = true;
+  for (int l = h->base; l <= finest(h); ++l) {
+    DevLevel& L = h->L[l];
+    const int i = l - h->base;
+    const long long n = cells_of(L.G);
+    const double* base = h->stage + L.stage_off;
+    if (phi && phi[i])
+      CK(cudaMemcpyAsync(phi[i], base, n * sizeof(double), cudaMemcpyDeviceToHost, h->cs));
+    for (int a = 0; disp && a < 3; ++a)
+      if (disp[3 * i + a])
+        CK(cudaMemcpyAsync(disp[3 * i + a], base + (a + 1) * n, n * sizeof(double),
+                           cudaMemcpyDeviceToHost, h->cs));
+  }
+  CK(cudaEventRecord(h->ev_copied, h->cs));
+  return MG_OK;
+}
+
+// Orders the work stream after the staged copies: before the stage is written
+// again and before the caller is told that the results are in host memory.
+mg_status join_copies(mg_hierarchy* h) {
+  if (!h->copies_pending) return MG_OK;
+  h->copies_pending = false;
+  const cudaError_t e = cudaStreamWaitEvent(h->s, h->ev_copied, 0);
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(h->cs);  // no copy may outlive the call
+    return fail_cuda(h, e, "cudaStreamWaitEvent(copies)");
+  }
+  return MG_OK;
+}
+
 // Orders the hierarchy's work stream after the caller's stream, runs f, then
 // orders the caller's stream after the work.
 template <typename F>
@@ -1491,10 +1552,14 @@ mg_status batch_pipeline(mg_batch* b, bool host, const double* const* const delt
   for (size_t i = 0; i < n; ++i) {
     mg_hierarchy* h = b->m[i];
     mg_status r = MG_OK;
-    if (phi1 && phi1[i])
-      for (int l = h->base; l <= finest(h) && r == MG_OK; ++l)
-        if (phi1[i][l - h->base]) r = store_leaf(h, l, phi_of(h->L[l]), phi1[i][l - h->base], host);
-    if (r == MG_OK && disp1 && disp1[i]) r = gradient_out(h, disp1[i], host, true);
+    if (host) {
+      r = stage_outputs(h, phi1 ? phi1[i] : nullptr, disp1 ? disp1[i] : nullptr);
+    } else {
+      if (phi1 && phi1[i])
+        for (int l = h->base; l <= finest(h) && r == MG_OK; ++l)
+          if (phi1[i][l - h->base]) r = store_leaf(h, l, phi_of(h->L[l]), phi1[i][l - h->base], host);
+      if (r == MG_OK && disp1 && disp1[i]) r = gradient_out(h, disp1[i], host, true);
+    }
     if (r == MG_OK) r = tau_into_f(h);
     if (r != MG_OK) return member_status(b, (int)i, r);
   }
@@ -1507,6 +1572,10 @@ mg_status batch_pipeline(mg_batch* b, bool host, const double* const* const delt
       for (int l = h->base; l <= finest(h) && r == MG_OK; ++l)
         if (phi2[i][l - h->base]) r = store_leaf(h, l, phi_of(h->L[l]), phi2[i][l - h->base], host);
     if (r == MG_OK && disp2 && disp2[i]) r = gradient_out(h, disp2[i], host, true);
+    if (r != MG_OK) return member_status(b, (int)i, r);
+  }
+  for (size_t i = 0; i < n; ++i) {
+    mg_status r = join_copies(b->m[i]);
     if (r != MG_OK) return member_status(b, (int)i, r);
   }
   for (size_t i = 0; i < n; ++i) BCK(cudaStreamSynchronize(b->m[i]->s));
@@ -1585,12 +1654,14 @@ mg_status job_advance(PipelineJob* j) {
   if (e != MG_OK && e != MG_ENOCONV) return e;
   j->res[k] = e;
   if (j->phase == 1) {
-    ST(job_store(j, j->phi1, j->disp1));
+    ST(stage_outputs(h, j->phi1.empty() ? nullptr : j->phi1.data(),
+                     j->disp1.empty() ? nullptr : j->disp1.data()));
     ST(tau_into_f(h));
     j->phase = 2;
     return job_begin_solve(j);
   }
   ST(job_store(j, j->phi2, j->disp2));
+  ST(join_copies(h));
   j->phase = 3;
   return job_record(j);
 }
@@ -1599,6 +1670,8 @@ void job_finish(PipelineJob* j, mg_status st) {
   if (st != MG_OK) {
     // nothing may still write the caller's buffers once the job reports
     cudaStreamSynchronize(j->h->s);
+    cudaStreamSynchronize(j->h->cs);
+    j->h->copies_pending = false;
     j->status = st;
   } else {
     j->status = j->res[0] != MG_OK ? j->res[0] : j->res[1];
@@ -1751,6 +1824,10 @@ mg_status mg_batch_lpt_pipeline(mg_batch* b, int host_buffers, const double* con
   for (mg_hierarchy* h : b->m) BCK(cudaStreamWaitEvent(h->s, b->ev_in, 0));
   const mg_status st = batch_pipeline(b, host, delta, phi1, phi2, disp1, disp2, info1, info2);
   for (mg_hierarchy* h : b->m) {
+    if (h->copies_pending) {  // a failed member left staged copies: let them finish
+      cudaStreamSynchronize(h->cs);
+      h->copies_pending = false;
+    }
     BCK(cudaEventRecord(h->ev_out, h->s));
     BCK(cudaStreamWaitEvent(b->user_s, h->ev_out, 0));
   }
@@ -1889,8 +1966,11 @@ mg_status mg_hierarchy_create(const mg_config* cfg, void* cuda_stream, mg_hierar
   h->user_s = (cudaStream_t)cuda_stream;
   h->base = plan.base;
   if (cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->cs, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_staged, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_copied, cudaEventDisableTiming) != cudaSuccess) {
     mg_hierarchy_destroy(h);
     return MG_ECUDA;
   }
@@ -1979,6 +2059,10 @@ mg_status mg_hierarchy_destroy(mg_hierarchy* h) {
     for (cudaEvent_t e : h->ev_start[f]) cudaEventDestroy(e);
     for (cudaEvent_t e : h->ev_end[f]) cudaEventDestroy(e);
   }
+  if (h->cs) cudaStreamSynchronize(h->cs);
+  if (h->ev_staged) cudaEventDestroy(h->ev_staged);
+  if (h->ev_copied) cudaEventDestroy(h->ev_copied);
+  if (h->cs) cudaStreamDestroy(h->cs);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->ev_out) cudaEventDestroy(h->ev_out);
   if (h->s) cudaStreamDestroy(h->s);
@@ -2118,22 +2202,32 @@ mg_status mg_lpt_pipeline(mg_hierarchy* h, int host_buffers, const double* const
       return fail(h, MG_EINVAL, "device displacement outputs must all be set");
   }
   return on_streams(h, [&]() -> mg_status {
-    for (int l = h->base; l <= finest(h); ++l) ST(load_leaf(h, l, delta[l - h->base], h->L[l].f, host));
-    mg_status st1 = solve_prepared(h, info1);
-    if (st1 != MG_OK && st1 != MG_ENOCONV) return st1;
-    if (phi1)
+    auto steps = [&]() -> mg_status {
       for (int l = h->base; l <= finest(h); ++l)
-        if (phi1[l - h->base]) ST(store_leaf(h, l, phi_of(h->L[l]), phi1[l - h->base], host));
-    if (disp1) ST(gradient_out(h, disp1, host, true));
-    ST(tau_into_f(h));
-    mg_status st2 = solve_prepared(h, info2);
-    if (st2 != MG_OK && st2 != MG_ENOCONV) return st2;
-    if (phi2)
-      for (int l = h->base; l <= finest(h); ++l)
-        if (phi2[l - h->base]) ST(store_leaf(h, l, phi_of(h->L[l]), phi2[l - h->base], host));
-    if (disp2) ST(gradient_out(h, disp2, host, true));
+        ST(load_leaf(h, l, delta[l - h->base], h->L[l].f, host));
+      mg_status st1 = solve_prepared(h, info1);
+      if (st1 != MG_OK && st1 != MG_ENOCONV) return st1;
+      if (host) {
+        ST(stage_outputs(h, phi1, disp1));
+      } else {
+        if (phi1)
+          for (int l = h->base; l <= finest(h); ++l)
+            if (phi1[l - h->base]) ST(store_leaf(h, l, phi_of(h->L[l]), phi1[l - h->base], host));
+        if (disp1) ST(gradient_out(h, disp1, host, true));
+      }
+      ST(tau_into_f(h));
+      mg_status st2 = solve_prepared(h, info2);
+      if (st2 != MG_OK && st2 != MG_ENOCONV) return st2;
+      if (phi2)
+        for (int l = h->base; l <= finest(h); ++l)
+          if (phi2[l - h->base]) ST(store_leaf(h, l, phi_of(h->L[l]), phi2[l - h->base], host));
+      if (disp2) ST(gradient_out(h, disp2, host, true));
+      return st1 != MG_OK ? st1 : st2;
+    };
+    const mg_status st = steps();
+    const mg_status j = join_copies(h);
     CK(cudaStreamSynchronize(h->s));
-    return st1 != MG_OK ? st1 : st2;
+    return (st != MG_OK && st != MG_ENOCONV) ? st : (j != MG_OK ? j : st);
   });
 }
 

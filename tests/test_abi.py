@@ -88,11 +88,11 @@ def test_workspace_grows_with_nests(mg):
     base = mg.workspace_bytes(mg.make_config((128,) * 3, 100.0, 6))
     deep = mg.workspace_bytes(mg.config_from_geometry(config_deep_zoom()))
     assert 0 < base < one < deep
-    # per 128^3 leaf level: float64 u (x2), f_fas and f on the padded grid; plus three dense
-    # staging arrays and three padded 2LPT work arrays of one level, and the (smaller)
-    # coarsenings below the base
+    # per 128^3 leaf level: float64 u (x2), f_fas and f on the padded grid, and four dense
+    # arrays staging the first solve's host outputs; plus three dense scratch arrays and
+    # three padded 2LPT work arrays of one level, and the (smaller) coarsenings below the base
     padded = 136 * 134 * 134
-    per_level = 4 * 8 * padded
+    per_level = 4 * 8 * padded + 4 * 8 * 128 ** 3
     assert deep < (5 * per_level + 3 * 8 * 128 ** 3 + 3 * 8 * padded) * 1.1
 
 

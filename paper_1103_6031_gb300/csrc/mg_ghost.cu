@@ -128,11 +128,16 @@ __global__ void __launch_bounds__(128)
 
 // One thread per fine column of a face; the 4 columns under one parent face
 // element are 4 consecutive lanes (a "quad"), which share the parent flux and
-// the mean of their fine fluxes through warp shuffles.
+// the mean of their fine fluxes through warp shuffles.  Scale factors come
+// precomputed (the float64 pipe is this kernel's bound): fc_scale = 1/(8 H) for the
+// covered parent cells (mean of 8 children, parent spacing H); the ghost shift
+// (F_c - mean F_f) h / c_side is a_side F_c - b_side (sum of the 4 unscaled fine
+// flux stencils), a_side = h / c_side, b_side = 1 / (4 c_side) (c_side: the sum of
+// the flux weights on the ghost side).
 template <int ORDER, typename T>
 __global__ void __launch_bounds__(128)
     k_cf_flux(Grid F, T* __restrict__ u, FaceSet fs, CfWeights w, const T* __restrict__ inter,
-              const T* __restrict__ fc_unc, T h, T invh, T invH, int flux_fix) {
+              const T* __restrict__ fc_unc, T fc_scale, T a0, T a1, T b0, T b1, int flux_fix) {
   constexpr int half = ORDER / 2;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= 4 * fs.ebase[6]) return;
@@ -168,9 +173,9 @@ __global__ void __launch_bounds__(128)
     T pair = u[in0 + (2 * d) * step] + u[in0 + (2 * d + 1) * step];
     pair += __shfl_xor_sync(quad, pair, 1);
     pair += __shfl_xor_sync(quad, pair, 2);
-    cov = fma(T(w.flux[s]), pair * T(0.125), cov);
+    cov = fma(T(w.flux[s]), pair, cov);
   }
-  const T fc = fma(cov, invH, fc_unc[e]);
+  const T fc = fma(cov, fc_scale, fc_unc[e]);
   T cq[half];
 #pragma unroll
   for (int q = 0; q < half; ++q) cq[q] = inter[fs.base[f] + ((long long)q * nt0 + tj) * nt1 + tk];
@@ -192,11 +197,10 @@ __global__ void __launch_bounds__(128)
     else x = s < half ? v[half - 1 - s] : ghost[s - half];
     ff = fma(T(w.flux[s]), x, ff);
   }
-  ff *= invh;
   ff += __shfl_xor_sync(quad, ff, 1);
   ff += __shfl_xor_sync(quad, ff, 2);
   T shift = T(0);
-  if (flux_fix) shift = (fc - T(0.25) * ff) * h / T(w.ghost_coef[side]);
+  if (flux_fix) shift = fma(-(side ? b1 : b0), ff, fc * (side ? a1 : a0));
 #pragma unroll
   for (int m = 0; m < half; ++m) u[in0 - (m + 1) * step] = ghost[m] + shift;
 }
@@ -266,10 +270,13 @@ cudaError_t launch_cf_flux(int order, const Grid& F, T* u, const FaceSet& fs, co
                            int flux_fix, cudaStream_t s) {
   const int block = 128;
   const unsigned grid = (unsigned)((4 * fs.ebase[6] + block - 1) / block);
+  const T fc_scale = T(0.125 * invH);
+  const T a0 = T(h / w.ghost_coef[0]), a1 = T(h / w.ghost_coef[1]);
+  const T b0 = T(0.25 * invh * h / w.ghost_coef[0]), b1 = T(0.25 * invh * h / w.ghost_coef[1]);
   switch (order) {
-    case 2: k_cf_flux<2, T><<<grid, block, 0, s>>>(F, u, fs, w, inter, fc_unc, T(h), T(invh), T(invH), flux_fix); break;
-    case 4: k_cf_flux<4, T><<<grid, block, 0, s>>>(F, u, fs, w, inter, fc_unc, T(h), T(invh), T(invH), flux_fix); break;
-    case 6: k_cf_flux<6, T><<<grid, block, 0, s>>>(F, u, fs, w, inter, fc_unc, T(h), T(invh), T(invH), flux_fix); break;
+    case 2: k_cf_flux<2, T><<<grid, block, 0, s>>>(F, u, fs, w, inter, fc_unc, fc_scale, a0, a1, b0, b1, flux_fix); break;
+    case 4: k_cf_flux<4, T><<<grid, block, 0, s>>>(F, u, fs, w, inter, fc_unc, fc_scale, a0, a1, b0, b1, flux_fix); break;
+    case 6: k_cf_flux<6, T><<<grid, block, 0, s>>>(F, u, fs, w, inter, fc_unc, fc_scale, a0, a1, b0, b1, flux_fix); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

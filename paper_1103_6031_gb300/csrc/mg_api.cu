@@ -259,6 +259,7 @@ struct mg_hierarchy {
   LoopGraph loop;
   LoopState* loop_dev = nullptr;
   LoopState* loop_host = nullptr;  // pinned copy written at the end of the loop graph
+  LoopState* loop_host1 = nullptr;  // pinned: the first solve's record in a pipeline
   // launch counters and optional CUDA-event timing per kernel family
   mg_stats stats;
   unsigned prof_mask = 0;    // families the caller asked to time
@@ -1114,8 +1115,8 @@ mg_status loop_launch(mg_hierarchy* h) {
 
 // The loop graph has finished: its record into st (as the host loop leaves it) and
 // its launches into the statistics.
-mg_status loop_read(mg_hierarchy* h, SolveState& st) {
-  const LoopState& R = *h->loop_host;
+mg_status loop_read(mg_hierarchy* h, SolveState& st, const LoopState* rec = nullptr) {
+  const LoopState& R = rec ? *rec : *h->loop_host;
   std::memset(&st.local, 0, sizeof(st.local));
   st.local.cycles = R.c;
   for (int i = 0; i < R.c && i < MG_MAX_HISTORY; ++i) st.local.history[i] = R.history[i];
@@ -1580,6 +1581,58 @@ mg_status batch_pipeline(mg_batch* b, bool host, const double* const* const delt
   }
   for (size_t i = 0; i < n; ++i) BCK(cudaStreamSynchronize(b->m[i]->s));
   return st1 != MG_OK ? st1 : st2;
+}
+
+}  // namespace
+
+// ---- the whole pipeline without a host round trip (MG_FLAG_DEVICE_LOOP) ----------
+//
+// With both solves' iteration loops on the device nothing in mg_lpt_pipeline needs a
+// value on the host before the end: the loads, the first loop graph, a copy of its
+// record, the first outputs, tau, the second loop graph and the second outputs are
+// all queued at once and the host waits once.  The records are read afterwards.
+
+namespace {
+
+mg_status pipeline_device_loops(mg_hierarchy* h, bool host, const double* const delta[],
+                                double* const phi1[], double* const phi2[],
+                                double* const disp1[], double* const disp2[], mg_info* info1,
+                                mg_info* info2) {
+  if (!h->loop_host1)
+    CK(cudaHostAlloc(&h->loop_host1, sizeof(LoopState), cudaHostAllocDefault));
+  for (int l = h->base; l <= finest(h); ++l)
+    ST(load_leaf(h, l, delta[l - h->base], h->L[l].f, host));
+  SolveState st1, st2;
+  ST(solve_begin(h));
+  ST(solve_begin_read(h, st1));
+  ST(loop_launch(h));
+  CK(cudaMemcpyAsync(h->loop_host1, h->loop_dev, sizeof(LoopState), cudaMemcpyDeviceToHost, h->s));
+  if (h->mixed) ST(gauge_zero_base_mean(h));
+  if (host) {
+    ST(stage_outputs(h, phi1, disp1));
+  } else {
+    if (phi1)
+      for (int l = h->base; l <= finest(h); ++l)
+        if (phi1[l - h->base]) ST(store_leaf(h, l, phi_of(h->L[l]), phi1[l - h->base], false));
+    if (disp1) ST(gradient_out(h, disp1, false, true));
+  }
+  ST(tau_into_f(h));
+  ST(solve_begin(h));
+  ST(solve_begin_read(h, st2));
+  ST(loop_launch(h));
+  if (h->mixed) ST(gauge_zero_base_mean(h));
+  if (phi2)
+    for (int l = h->base; l <= finest(h); ++l)
+      if (phi2[l - h->base]) ST(store_leaf(h, l, phi_of(h->L[l]), phi2[l - h->base], host));
+  if (disp2) ST(gradient_out(h, disp2, host, true));
+  CK(cudaStreamSynchronize(h->s));
+  ST(loop_read(h, st1, h->loop_host1));
+  const mg_status r1 = finish_info(h, st1.local, st1.rel, st1.at_floor, info1);
+  if (r1 != MG_OK && r1 != MG_ENOCONV) return r1;
+  ST(loop_read(h, st2));
+  const mg_status r2 = finish_info(h, st2.local, st2.rel, st2.at_floor, info2);
+  if (r2 != MG_OK && r2 != MG_ENOCONV) return r2;
+  return r1 != MG_OK ? r1 : r2;
 }
 
 }  // namespace
@@ -2053,6 +2106,7 @@ mg_status mg_hierarchy_destroy(mg_hierarchy* h) {
   if (h->loop.graph) cudaGraphDestroy(h->loop.graph);
   cudaFree(h->loop_dev);
   if (h->loop_host) cudaFreeHost(h->loop_host);
+  if (h->loop_host1) cudaFreeHost(h->loop_host1);
   hybrid_destroy(h->hybrid);
   cudaFree(h->hybrid_f);
   for (int f = 0; f < MG_K_FAMILIES; ++f) {
@@ -2200,6 +2254,15 @@ mg_status mg_lpt_pipeline(mg_hierarchy* h, int host_buffers, const double* const
     if (!check_ptrs((const void* const*)disp1, 3 * nleaf) ||
         !check_ptrs((const void* const*)disp2, 3 * nleaf))
       return fail(h, MG_EINVAL, "device displacement outputs must all be set");
+  }
+  if (device_loop_on(h)) {
+    return on_streams(h, [&]() -> mg_status {
+      const mg_status st = pipeline_device_loops(h, host, delta, phi1, phi2, disp1, disp2, info1,
+                                                 info2);
+      const mg_status j = join_copies(h);
+      CK(cudaStreamSynchronize(h->s));
+      return (st != MG_OK && st != MG_ENOCONV) ? st : (j != MG_OK ? j : st);
+    });
   }
   return on_streams(h, [&]() -> mg_status {
     auto steps = [&]() -> mg_status {

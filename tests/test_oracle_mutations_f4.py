@@ -3,8 +3,10 @@ must fail at least one of their pins (on the CPU, for the duration of one test):
 a wrong Philox multiplier, a missing key bump, a uniform without its half-unit
 offset, a Box-Muller pair built from one trigonometric function, a sign error in
 the finite-difference gradient symbol of the hybrid correction, a dropped factor i
-of the exact gradient, and density determinants with the sign of the Hessian or
-the mixed derivatives wrong.
+of the exact gradient, density determinants with the sign of the Hessian or the
+mixed derivatives wrong, and in the multi-scale density a non-conservative or
+mirrored tricubic interpolation, Hoffman-Ribak without its 1/sqrt(8), a convolution
+without the cell-volume factor and a nest without the parent's long waves.
 """
 
 import numpy as np
@@ -115,3 +117,55 @@ def test_lla_without_mixed_derivatives_is_caught(monkeypatch):
 
     monkeypatch.setattr(lpt, "second_derivatives", no_mixed)
     _fails(t_lla.test_diagonal_mode, 6)
+
+
+# ---- multi-scale density (Sec. 2.3) ----
+
+import oracle.density as dens  # noqa: E402
+from tests import test_oracle_density as t_dens  # noqa: E402
+
+
+def test_tricubic_without_conservation_is_caught(monkeypatch):
+    # no shift restoring each parent's mean: the plain tricubic values
+    monkeypatch.setattr(dens, "inject", lambda c: np.zeros(tuple(2 * m for m in c.shape)))
+    _fails(t_dens.test_tricubic_conservative_interpolation)
+
+
+def test_tricubic_with_swapped_parities_is_caught(monkeypatch):
+    good = dens.cubic_weights
+
+    def swapped(t):
+        return good(1.0 - t)
+
+    monkeypatch.setattr(dens, "cubic_weights", swapped)
+    _fails(t_dens.test_tricubic_conservative_interpolation)
+
+
+def test_hoffman_ribak_without_rescaling_is_caught(monkeypatch):
+    def unscaled(geom, seed):
+        mu = [noise.white_noise(seed, int(np.prod(geom.base_n)), 0).reshape(tuple(geom.base_n))]
+        for lvl, nest in enumerate(geom.nests, start=1):
+            own = noise.white_noise(seed, int(np.prod(nest.n)), lvl).reshape(tuple(nest.n))
+            mu.append(own - dens.inject(dens.children_mean(own))
+                      + dens.inject(mu[-1][dens._region(nest)]))     # missing 1/sqrt(8)
+        return mu
+
+    monkeypatch.setattr(t_dens, "level_noise", unscaled)
+    _fails(t_dens.test_hoffman_ribak_constraint_and_variance)
+
+
+def test_convolution_without_cell_volume_factor_is_caught(monkeypatch):
+    good = dens.convolve_periodic
+
+    def no_volume(noise_, h, sqrt_p, dk):
+        return good(noise_, h, sqrt_p, dk) * h ** 1.5
+
+    monkeypatch.setattr(dens, "convolve_periodic", no_volume)
+    _fails(t_dens.test_single_level_is_the_periodic_field)
+
+
+def test_nest_without_the_parent_contribution_is_caught(monkeypatch):
+    good = dens.tricubic_conservative
+    monkeypatch.setattr(dens, "tricubic_conservative",
+                        lambda parent, off, n: np.zeros_like(good(parent, off, n)))
+    _fails(t_dens.test_nest_carries_the_parent_large_scales)

@@ -101,7 +101,6 @@ def workload_config(geom, name="zoom2"):
     return {"workload": WORKLOAD_TEXT[name],
             "level_cells": geom.level_cells(), "order": geom.order, "levels": geom.n_levels,
             "solve_tol": WORKLOAD_TOL[name], "precision": "fp64",
-            "iteration_loop": "on the device (MG_FLAG_DEVICE_LOOP): one host wait per step",
             "l2": "256 MiB flush written between timed steps, outside the per-step events"}
 
 
@@ -864,6 +863,8 @@ def run_ours(args):
                          "share_of_step": total_smooth_ms / max(sum(step_ms) / len(step_ms), 1e-9),
                          "share_of_kernel_time": share_kernel_time},
             "gpu_launches": launches,
+            "iteration_loop": ("host (profiling run)" if args.profile_run else
+                               "on the device (MG_FLAG_DEVICE_LOOP): one host wait per step"),
             "clocks": clocks,
             "mixed_precision": mixed,
             "batched": batched,

@@ -317,7 +317,9 @@ mg_status mg_server_get_stats(mg_server* s, mg_server_stats* out);
 
 /* Stops taking requests, fails the ones not yet started (status MG_EINVAL,
  * "server closed"), waits for the running ones, frees every hierarchy.
- * NULL-safe.  Results not yet polled are dropped. */
+ * NULL-safe.  Results not yet polled are dropped.  No other mg_server_* call on
+ * the same server may run concurrently with it (submit, poll and get_stats may
+ * otherwise be called from any threads at once). */
 mg_status mg_server_destroy(mg_server* s);
 
 /* Kernel families for launch counting and event timing. */

@@ -101,3 +101,24 @@ def test_batch_geometries_are_all_valid(mg):
         cfg = mg.config_from_geometry(geom)
         st, msg = mg.validate(cfg)
         assert st == 0, (geom, msg)
+
+
+def test_null_handles_and_bad_arguments_are_rejected_without_a_gpu(mg):
+    """Argument checks that run before any CUDA call: NULL handles and impossible
+    sizes give MG_EINVAL (or -1 from mg_server_poll), destroy calls are NULL-safe."""
+    lib = mg.load_library()
+    out = ctypes.c_void_p()
+    assert lib.mg_server_create(0, 4, ctypes.byref(out)) == 1          # no budget
+    assert lib.mg_server_create(1 << 30, 0, ctypes.byref(out)) == 1    # no request slot
+    assert lib.mg_server_create(1 << 30, 257, ctypes.byref(out)) == 1  # too many
+    assert lib.mg_server_create(1 << 30, 4, None) == 1
+    cfg = mg.make_config((32, 32, 32), 1.0, 2)
+    assert lib.mg_server_submit(None, 0, ctypes.byref(cfg), None, None, None, None, None) == 1
+    assert lib.mg_server_poll(None, None, 1, 0.0) == -1
+    assert lib.mg_server_get_stats(None, None) == 1
+    assert lib.mg_server_destroy(None) == 0
+    assert lib.mg_hierarchy_destroy(None) == 0
+    assert lib.mg_batch_destroy(None) == 0
+    assert lib.mg_batch_create(None, 0, None, ctypes.byref(out)) == 1
+    assert lib.mg_hierarchy_create(None, None, ctypes.byref(out)) == 1
+    assert lib.mg_last_error(None) in (b"", None)

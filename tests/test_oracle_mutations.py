@@ -4,7 +4,8 @@ Each test patches one plausible error into the oracle (on the CPU, for the
 duration of the test only) and checks that the pin written for that part of
 the method catches it: a transposed interpolation weight, a dropped flux
 term, a wrong restriction, a shifted injection, a reversed gradient, a wrong
-mixed derivative, a wrong smoother diagonal.
+mixed derivative, a wrong smoother diagonal, a cubic volume in the composite mean,
+edge ghosts without their tensor cross-terms.
 """
 
 import numpy as np
@@ -114,3 +115,47 @@ def test_mixed_derivative_as_product_is_caught(monkeypatch):
 
     monkeypatch.setattr(lpt, "second_derivatives", product_of_gradients)
     _fails(t_lpt.test_tau_diagonal_mode_closed_form, 2)
+
+
+def test_cubic_volume_in_composite_mean_is_caught(monkeypatch):
+    """The composite mean divided by box^3 instead of the base's volume h^3 n0 n1 n2
+    agrees on cubic bases only; the non-cubic pins catch it."""
+    def box_cubed(hier, fields):
+        total = 0.0
+        for l, fld in zip(hier.leaf_levels(), fields):
+            total += hier.levels[l].h ** 3 * float(np.sum(fld[hier.uncovered_mask(l)]))
+        return total / hier.box ** 3
+
+    monkeypatch.setattr(mg, "composite_mean", box_cubed)
+    _fails(t_nested.test_constant_source_vanishes_on_noncubic_base, 4)
+    _fails(t_nested.test_prepared_source_has_zero_composite_integral_on_noncubic_base, 2)
+
+
+def _additive_edges(lev, U, tw, half):
+    """Edge and corner ghosts from the neighbouring face ghosts and interior cells,
+    u(x) = sum_a u(x with the other outside axes clamped) - (m - 1) u(all clamped):
+    exact for affine fields, wrong by the cross-terms of a product field."""
+    g, n = lev.g, lev.n
+    idx = [np.arange(-g, n[a] + g) for a in range(3)]
+    I = np.meshgrid(*idx, indexing="ij")
+    out = [(I[a] < 0) | (I[a] >= n[a]) for a in range(3)]
+    cl = [np.clip(I[a], 0, n[a] - 1) for a in range(3)]
+    count = out[0].astype(int) + out[1] + out[2]
+    sel = count >= 2
+    u = lev.u.copy()
+    acc = np.zeros(u.shape)
+    for a in range(3):
+        pos = [np.where(out[b] & (b != a), cl[b], I[b]) + g for b in range(3)]
+        acc += np.where(out[a], u[pos[0], pos[1], pos[2]], 0.0)
+    allc = [cl[b] + g for b in range(3)]
+    acc -= (count - 1) * u[allc[0], allc[1], allc[2]]
+    lev.u[sel] = acc[sel]
+
+
+def test_additive_edge_rule_is_caught(monkeypatch):
+    """Edges that drop the tensor cross-terms pass the affine pin but fail the
+    product-field pin."""
+    monkeypatch.setattr(hy, "_fill_edges", _additive_edges)
+    t_nested.test_edge_ghosts_exact_on_separable_polynomials(4)   # affine: still exact
+    _fails(t_nested.test_edge_ghosts_exact_on_tensor_linear_field, 4, False)
+    _fails(t_nested.test_edge_ghosts_exact_on_tensor_linear_field, 2, True)

@@ -280,3 +280,105 @@ def test_nested_solution_tends_to_unigrid_as_the_patch_grows(order, bound):
         errs.append(np.sqrt(np.mean(d ** 2) / np.mean((ref - ref.mean()) ** 2)))
     assert errs[0] > errs[1] > errs[2]
     assert errs[0] < bound
+
+
+# ---- non-cubic periodic base (the base's volume is h^3 n0 n1 n2, not box^3) --------
+
+def _noncubic(order, nest=True):
+    """24 x 32 x 40 periodic base (box = length of axis 0); optionally a nest of
+    16 x 20 x 24 cells (8 x 10 x 12 parent cells) with a margin of >= 6 parent cells."""
+    from synthetic import Geometry, NestSpec
+    nests = (NestSpec((16, 20, 24), (8, 11, 14)),) if nest else ()
+    return Geometry((24, 32, 40), 30.0, order, nests)
+
+
+@pytest.mark.parametrize("order", ORDERS)
+def test_prepared_source_has_zero_composite_integral_on_noncubic_base(order):
+    """After the mean removal (solvability of the periodic composite problem, reading
+    of Sec. 3.2) the volume-weighted sum of f over leaf cells vanishes, whatever the
+    aspect ratio of the base."""
+    from oracle.multigrid import prepare_source
+    geom = _noncubic(order)
+    hier = Hierarchy(geom)
+    rng = np.random.default_rng(21)
+    src = [rng.standard_normal(hier.levels[l].n) + 0.7 for l in hier.leaf_levels()]
+    mean = prepare_source(hier, src)
+    total = scale = 0.0
+    for l in hier.leaf_levels():
+        lev = hier.levels[l]
+        mask = hier.uncovered_mask(l)
+        total += lev.h ** 3 * np.sum(lev.f[mask])
+        scale += lev.h ** 3 * np.sum(np.abs(lev.f[mask]))
+    assert abs(total) < 1e-13 * scale
+    assert 0.5 < mean < 0.9   # the +0.7 offset, up to the noise's own mean
+
+
+@pytest.mark.parametrize("order", ORDERS)
+def test_constant_source_vanishes_on_noncubic_base(order):
+    """A constant source is its own composite mean: the prepared source is zero on
+    every level and the solve returns phi = 0 (to rounding)."""
+    from oracle.multigrid import prepare_source
+    geom = _noncubic(order)
+    hier = Hierarchy(geom)
+    c = 2.5
+    mean = prepare_source(hier, [np.full(hier.levels[l].n, c) for l in hier.leaf_levels()])
+    assert abs(mean - c) < 1e-14 * c
+    for l in hier.leaf_levels():
+        assert np.max(np.abs(hier.levels[l].f)) < 1e-13 * c
+    phis, _ = solve(geom, [np.full(hier.levels[l].n, c) for l in hier.leaf_levels()], cycles=2)
+    for p in phis:
+        assert np.max(np.abs(p)) < 1e-10
+
+
+@pytest.mark.parametrize("order", ORDERS)
+def test_noncubic_single_level_fas_reaches_exact_dft_solve(order):
+    """On one periodic 24 x 32 x 40 level the FAS iteration reaches the DFT solve of
+    the same discrete operator (the plain definition of the result)."""
+    geom = _noncubic(order, nest=False)
+    rng = np.random.default_rng(5)
+    f = rng.standard_normal(geom.base_n) + 0.3
+    phis, info = solve(geom, [f], tol=1e-13, max_cycles=40)
+    ex = exact_solve(f - f.mean(), geom.box / geom.base_n[0], order)
+    rel = np.sqrt(np.mean((phis[0] - ex) ** 2) / np.mean(ex ** 2))
+    assert rel < 1e-12
+    hier = info["hierarchy"]
+    assert abs(hier.levels[hier.base].f.mean()) < 1e-14
+
+
+@pytest.mark.parametrize("order", ORDERS)
+def test_noncubic_nested_convergence_rate(order):
+    geom = _noncubic(order)
+    d = make_delta(geom, 9)
+    phis, info = solve(geom, d, tol=1e-12, max_cycles=30)
+    assert info["rel_residual"] <= 1e-12
+    reduction = _claims()["min_reduction_per_cycle_nested"]
+    hist = info["history"]
+    for a, b in zip(hist[:-1], hist[1:]):
+        assert a / b >= reduction, hist
+
+
+# ---- edge and corner ghosts on a field with tensor cross-terms ---------------------
+
+def _tensor_linear(X, Y, Z):
+    """A product of per-axis linear factors: its 8-child mean equals its value at the
+    parent centre, so covered parent cells stay exact after the two-way sync, while the
+    cross-terms xy, yz, xz, xyz are non-zero (an additive edge rule is not exact)."""
+    return (0.4 + 1.3 * X) * (0.9 - 1.1 * Y) * (-0.6 + 0.8 * Z)
+
+
+@pytest.mark.parametrize("order", ORDERS)
+@pytest.mark.parametrize("noncubic", [False, True])
+def test_edge_ghosts_exact_on_tensor_linear_field(order, noncubic):
+    """Every ghost of a nest (faces after the flux step, edges and corners by tensor
+    interpolation of parent data, reading R10) reproduces a field that is linear along
+    each axis, including its mixed terms, which the mixed derivatives of the 2LPT source
+    (Sec. 3.1.2) read at the edges."""
+    geom = _noncubic(order) if noncubic else small_zoom(24, ((20, 7),), order=order, box=1.0)
+    hier = Hierarchy(geom)
+    _fill_with(hier, hier.base, _tensor_linear)
+    origin = _fill_with(hier, hier.finest, _tensor_linear)
+    lev = hier.levels[hier.finest]
+    fill_ghosts(hier, hier.finest, edges=True, flux_fix=True)
+    X, Y, Z = _centres(lev, origin, extra=lev.g)
+    expect = _tensor_linear(X, Y, Z)
+    np.testing.assert_allclose(lev.u, expect, atol=1e-12)

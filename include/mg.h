@@ -121,6 +121,11 @@ typedef struct {
   double source_mean;                  /* composite mean removed from the source        */
   double history[MG_MAX_HISTORY];      /* rel_residual after each cycle                 */
   int inner_cycles;                    /* MG_MIXED: float32 V-cycles run in total       */
+  /* after the last cycle, per leaf level l (0 = base, i = nest i-1): the volume-weighted
+   * L2 norm of f - L u over that level's leaf cells divided by the same norm of its f
+   * (the norm itself where the level's f is zero); entries >= n_levels are 0.  The
+   * largest entry shows where the composite residual sits (Sec. 3.2 stopping rule). */
+  double level_rel_residual[MG_MAX_LEVELS];
 } mg_info;
 
 /* Fill *cfg with defaults: order 2, FP64, nu1 = nu2 = 2, max_cycles 50,

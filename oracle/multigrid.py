@@ -89,8 +89,12 @@ def sync_covered(hier):
         hier.levels[l - 1].interior[hier.covered_region(l)] = restrict(hier.levels[l].interior)
 
 
-def leaf_residual_norms(hier, flux_fix=True):
-    """(sqrt(sum h^3 r^2), sqrt(sum h^3 f^2)) over leaf cells, after sync."""
+def leaf_residual_norms(hier, flux_fix=True, per_level=None):
+    """(sqrt(sum h^3 r^2), sqrt(sum h^3 f^2)) over leaf cells, after sync.
+
+    If per_level is a list, the pair (sum h^3 r^2, sum h^3 f^2) of every leaf level
+    (base first) is appended to it: the per-level view of the same norm (reading of
+    the "norm of the residual" stopping rule, Sec. 3.2)."""
     sync_covered(hier)
     num = den = 0.0
     for l in hier.leaf_levels():
@@ -99,9 +103,18 @@ def leaf_residual_norms(hier, flux_fix=True):
         r = lev.f - laplacian(lev)
         mask = hier.uncovered_mask(l)
         vol = lev.h ** 3
-        num += vol * float(np.sum(r[mask] ** 2))
-        den += vol * float(np.sum(lev.f[mask] ** 2))
+        rr = vol * float(np.sum(r[mask] ** 2))
+        ff = vol * float(np.sum(lev.f[mask] ** 2))
+        num += rr
+        den += ff
+        if per_level is not None:
+            per_level.append((rr, ff))
     return np.sqrt(num), np.sqrt(den)
+
+
+def level_relative_residuals(pairs):
+    """sqrt(rr) / sqrt(ff) per leaf level (the residual norm itself where ff = 0)."""
+    return [np.sqrt(rr) / np.sqrt(ff) if ff > 0 else np.sqrt(rr) for rr, ff in pairs]
 
 
 def composite_mean(hier, fields):
@@ -141,13 +154,16 @@ def solve(geom_or_hier, sources, tol=1e-10, max_cycles=50, nu1=2, nu2=2, cycles=
     history = []
     limit = cycles if cycles is not None else max_cycles
     rel = np.inf
+    levels = []
     for _ in range(limit):
         vcycle(hier, hier.finest, nu1, nu2, flux_fix)
-        rnorm, fnorm = leaf_residual_norms(hier, flux_fix)
+        pairs = []
+        rnorm, fnorm = leaf_residual_norms(hier, flux_fix, per_level=pairs)
         rel = rnorm / fnorm if fnorm > 0 else rnorm
         history.append(rel)
+        levels = level_relative_residuals(pairs)
         if cycles is None and rel <= tol:
             break
     phis = [hier.levels[l].interior.copy() for l in hier.leaf_levels()]
     return phis, {"cycles": len(history), "rel_residual": rel, "history": history,
-                  "hierarchy": hier}
+                  "level_rel_residual": levels, "hierarchy": hier}

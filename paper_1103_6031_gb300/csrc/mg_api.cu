@@ -80,6 +80,8 @@ Bufs<float>& bufs<float>(DevLevel& L) {
 }
 
 constexpr size_t kAlign = 256;
+// doubles of the reduction record: norm sums, source sum, wait flag, per-level norm sums
+constexpr int kRedDoubles = 8 + 2 * MG_MAX_LEVELS;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
@@ -137,7 +139,14 @@ struct LoopState {
   double source_mean;
   double history[MG_MAX_HISTORY];
   unsigned char inner_hist[MG_MAX_HISTORY];  // MG_MIXED: inner cycles per iteration
+  double level_rel[MG_MAX_LEVELS];           // per leaf level, after the last iteration
 };
+
+// The relative residual of one leaf level from its volume-weighted sums of r^2 and f^2
+// (the residual norm itself when the level's source is zero).
+__host__ __device__ inline double level_relative(double rr, double ff) {
+  return ff > 0.0 ? sqrt(rr) / sqrt(ff) : sqrt(rr);
+}
 
 __host__ __device__ inline int inner_plan(int cap, double tol, double rel_before, double rel_after,
                                           int used) {
@@ -156,6 +165,7 @@ struct LoopParams {
   int max_cycles;
   int mixed;
   int cap;
+  int n_leaf;  // leaf levels (base and nests): red[8 + 2 l], red[9 + 2 l] hold level l's sums
 };
 
 __global__ void k_loop_init(LoopState* st, int mixed, int cap) {
@@ -186,6 +196,7 @@ __global__ void k_loop_step(LoopState* st, const double* red, LoopParams p,
     st->inner_now = inner_plan(p.cap, p.tol, before, rel, st->inner_now);
   }
   if (c < MG_MAX_HISTORY) st->history[c] = rel;
+  for (int l = 0; l < p.n_leaf; ++l) st->level_rel[l] = level_relative(red[8 + 2 * l], red[9 + 2 * l]);
   st->c = c + 1;
   const bool fixed = !(p.tol > 0.0);
   const double mean = st->source_mean;
@@ -238,8 +249,10 @@ struct mg_hierarchy {
   size_t arena_bytes = 0;
   double* partial = nullptr;
   int partial_slots = 0;
-  double* red = nullptr;       // [0..1] norm sums, [2..3] source sum, [4] wait flag
-  double* host_red = nullptr;  // pinned copy of red[0..4]
+  // [0..1] norm sums, [2..3] source sum, [4] wait flag, [8 + 2 l, 9 + 2 l] the norm
+  // sums of leaf level l (kRedDoubles in all)
+  double* red = nullptr;
+  double* host_red = nullptr;  // pinned copy of red
   unsigned* wait_err = nullptr;  // device flag: a bounded wait in a kernel ran out
   double* scratch = nullptr;   // 3 dense arrays of the largest leaf level
   long long scratch_elems = 0;
@@ -440,7 +453,7 @@ size_t carve(const mg_config* cfg, const Plan& p, mg_hierarchy* h, char* arena) 
     }
   }
   double* partial = c.take<double>((size_t)slots * 2);
-  double* red = c.take<double>(8);
+  double* red = c.take<double>(kRedDoubles);
   double* scratch = c.take<double>((size_t)3 * max_leaf);
   double* tau_work = c.take<double>((size_t)3 * max_leaf_padded);
   double* stage = c.take<double>((size_t)4 * leaf_total);
@@ -679,6 +692,17 @@ mg_status sync_covered(mg_hierarchy* h) {
   return MG_OK;
 }
 
+// Partial-sum slots of every leaf level (base first).
+LevelRanges leaf_ranges(const mg_hierarchy* h) {
+  LevelRanges R{};
+  R.n = finest(h) - h->base + 1;
+  for (int l = h->base; l <= finest(h); ++l) {
+    R.off[l - h->base] = h->L[l].partial_off;
+    R.cnt[l - h->base] = h->L[l].nblocks;
+  }
+  return R;
+}
+
 // Leaf residual norm after syncing covered cells, queued on the stream (no
 // host synchronisation, so it can be captured); ends with the copy of 4
 // doubles to pinned host memory.  In MG_MIXED the residual is also stored
@@ -696,9 +720,10 @@ mg_status norm_launches(mg_hierarchy* h, bool zero_u = false, bool copy_out = tr
                            h->mixed ? L.s.ffas : nullptr, h->s));
   }
   KL(MG_K_NORM, h->partial_slots,
-     launch_reduce_partials(h->partial, h->partial_slots, 2, h->red, h->s));
+     launch_reduce_levels(h->partial, h->partial_slots, leaf_ranges(h), h->red, h->red + 8, h->s));
   if (copy_out)
-    CK(cudaMemcpyAsync(h->host_red, h->red, 5 * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaMemcpyAsync(h->host_red, h->red, kRedDoubles * sizeof(double), cudaMemcpyDeviceToHost,
+                       h->s));
   return MG_OK;
 }
 
@@ -929,6 +954,9 @@ mg_status solve_step_read(mg_hierarchy* h, SolveState& st) {
     h->inner_now = next_inner_cycles(h, before, st.rel, h->inner_now);
   }
   record(st.local, st.rel);
+  for (int l = h->base; l <= finest(h); ++l)
+    st.local.level_rel_residual[l - h->base] =
+        mgloop::level_relative(h->host_red[8 + 2 * (l - h->base)], h->host_red[9 + 2 * (l - h->base)]);
   st.c++;
   const bool fixed = !(h->cfg.tol > 0.0);
   // A source that is constant up to rounding (zero after the mean removal but for
@@ -1050,6 +1078,7 @@ mg_status build_loop_graph(mg_hierarchy* h) {
   lp.max_cycles = h->cfg.max_cycles;
   lp.mixed = mixed;
   lp.cap = cap;
+  lp.n_leaf = finest(h) - h->base + 1;
   const double* red = h->red;
   auto step = [&](mg_hierarchy* hh) -> mg_status {
     mgloop::k_loop_step<<<1, 1, 0, hh->s>>>(dev, red, lp, while_h, switch_h);
@@ -1122,6 +1151,8 @@ mg_status loop_read(mg_hierarchy* h, SolveState& st, const LoopState* rec = null
   for (int i = 0; i < R.c && i < MG_MAX_HISTORY; ++i) st.local.history[i] = R.history[i];
   st.local.source_mean = R.source_mean;
   st.local.inner_cycles = R.inner_total;
+  for (int l = h->base; l <= finest(h); ++l)
+    st.local.level_rel_residual[l - h->base] = R.level_rel[l - h->base];
   st.rel = R.rel;
   st.at_floor = R.at_floor != 0;
   st.c = R.c;
@@ -2069,8 +2100,8 @@ mg_status mg_hierarchy_create(const mg_config* cfg, void* cuda_stream, mg_hierar
   }
   const LevelGeom& b = plan.geo[plan.base];
   h->volume = b.h * b.h * b.h * (double)b.n[0] * b.n[1] * b.n[2];
-  cudaError_t e = cudaMallocHost(&h->host_red, 8 * sizeof(double));
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->red, 0, 8 * sizeof(double), h->s);
+  cudaError_t e = cudaMallocHost(&h->host_red, kRedDoubles * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->red, 0, kRedDoubles * sizeof(double), h->s);
   if (e == cudaSuccess) e = setup_tma(h);
   if (e != cudaSuccess) {
     mg_hierarchy_destroy(h);

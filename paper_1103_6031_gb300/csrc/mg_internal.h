@@ -133,6 +133,16 @@ cudaError_t launch_sum_partial(const Grid& G, const double* f, double vol, Int3 
                                double* partial, int blocks, cudaStream_t s);
 cudaError_t launch_reduce_partials(const double* partial, int count, int width, double* out,
                                    cudaStream_t s);
+// Slots [off[l], off[l] + cnt[l]) of the partial-sum array belong to leaf level l.
+struct LevelRanges {
+  int n;
+  int off[MG_MAX_LEVELS];
+  int cnt[MG_MAX_LEVELS];
+};
+// out[0..1] = the sums of all `count` pairs (the same order as launch_reduce_partials);
+// out_levels[2 l .. 2 l + 1] = the sums of leaf level l's pairs.
+cudaError_t launch_reduce_levels(const double* partial, int count, const LevelRanges& R,
+                                 double* out, double* out_levels, cudaStream_t s);
 cudaError_t launch_pack(const Grid& G, const double* src, double* dst, double shift,
                         cudaStream_t s);
 // dense dst = padded interior of src + add

@@ -171,6 +171,30 @@ __global__ void __launch_bounds__(kRedBlock)
   }
 }
 
+// Block 0: exactly k_reduce_partials over all `count` pairs into out[0], out[1].
+// Block 1 + l: the pairs of leaf level l alone, [R.off[l], R.off[l] + R.cnt[l]), into
+// out_levels[2 l], out_levels[2 l + 1] (the per-level residual and source sums).
+__global__ void __launch_bounds__(kRedBlock)
+    k_reduce_levels(const double* __restrict__ partial, int count, LevelRanges R,
+                    double* __restrict__ out, double* __restrict__ out_levels) {
+  int lo = 0, hi = count;
+  if (blockIdx.x > 0) {
+    lo = R.off[blockIdx.x - 1];
+    hi = lo + R.cnt[blockIdx.x - 1];
+  }
+  double a = 0.0, b = 0.0;
+  for (int t = lo + threadIdx.x; t < hi; t += kRedBlock) {
+    a += partial[2 * t];
+    b += partial[2 * t + 1];
+  }
+  block_sum2<kRedBlock>(a, b);
+  if (threadIdx.x == 0) {
+    double* o = blockIdx.x == 0 ? out : out_levels + 2 * (blockIdx.x - 1);
+    o[0] = a;
+    o[1] = b;
+  }
+}
+
 __global__ void __launch_bounds__(256)
     k_pack(Grid G, const double* __restrict__ src, double* __restrict__ dst, double shift) {
   const long long n = (long long)G.n0 * G.n1 * G.n2;
@@ -411,6 +435,15 @@ cudaError_t launch_reduce_partials(const double* partial, int count, int width, 
                                    cudaStream_t s) {
   (void)width;
   k_reduce_partials<<<1, kRedBlock, 0, s>>>(partial, count, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_levels(const double* partial, int count, const LevelRanges& R,
+                                 double* out, double* out_levels, cudaStream_t s) {
+  if (R.n < 0 || R.n > MG_MAX_LEVELS) return cudaErrorInvalidValue;
+  for (int l = 0; l < R.n; ++l)
+    if (R.off[l] < 0 || R.cnt[l] < 0 || R.off[l] + R.cnt[l] > count) return cudaErrorInvalidValue;
+  k_reduce_levels<<<1 + R.n, kRedBlock, 0, s>>>(partial, count, R, out, out_levels);
   return cudaGetLastError();
 }
 

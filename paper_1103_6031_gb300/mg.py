@@ -56,12 +56,16 @@ class MGInfo(ctypes.Structure):
         ("source_mean", ctypes.c_double),
         ("history", ctypes.c_double * MG_MAX_HISTORY),
         ("inner_cycles", ctypes.c_int),
+        ("level_rel_residual", ctypes.c_double * MG_MAX_LEVELS),
     ]
 
-    def as_dict(self):
+    def as_dict(self, n_levels=MG_MAX_LEVELS):
+        """The record as a dict; level_rel_residual keeps the first n_levels entries
+        (the leaf levels, base first)."""
         return {"cycles": self.cycles, "rel_residual": self.rel_residual,
                 "source_mean": self.source_mean, "inner_cycles": self.inner_cycles,
-                "history": [self.history[i] for i in range(min(self.cycles, MG_MAX_HISTORY))]}
+                "history": [self.history[i] for i in range(min(self.cycles, MG_MAX_HISTORY))],
+                "level_rel_residual": [self.level_rel_residual[i] for i in range(n_levels)]}
 
 
 class MGServerResult(ctypes.Structure):
@@ -313,14 +317,14 @@ class Hierarchy:
         info = MGInfo()
         st = self.lib.mg_solve_1lpt(self.h, _ptrs(deltas, self.shapes), _ptrs(phis), ctypes.byref(info))
         self._check(st, "mg_solve_1lpt", allow_noconv)
-        return phis, info.as_dict()
+        return phis, info.as_dict(len(self.shapes))
 
     def solve_2lpt(self, phi1, allow_noconv=False):
         phis = [self._empty(s) for s in self.shapes]
         info = MGInfo()
         st = self.lib.mg_solve_2lpt(self.h, _ptrs(phi1, self.shapes), _ptrs(phis), ctypes.byref(info))
         self._check(st, "mg_solve_2lpt", allow_noconv)
-        return phis, info.as_dict()
+        return phis, info.as_dict(len(self.shapes))
 
     def lpt2_source(self, phi1):
         taus = [self._empty(s) for s in self.shapes]
@@ -371,7 +375,7 @@ class Hierarchy:
                                       _ptrs(outputs["disp2"], disp_shapes, host),
                                       ctypes.byref(i1), ctypes.byref(i2))
         self._check(st, "mg_lpt_pipeline", allow_noconv)
-        return outputs, i1.as_dict(), i2.as_dict()
+        return outputs, i1.as_dict(len(self.shapes)), i2.as_dict(len(self.shapes))
 
     def set_stream(self, stream):
         """Order later calls against `stream` (a torch.cuda.Stream)."""
@@ -454,7 +458,8 @@ class Batch:
         if not (st == 0 or (allow_noconv and st == 3)):
             msg = self.lib.mg_batch_last_error(self.b)
             raise MGError(st, "mg_batch_lpt_pipeline: " + (msg.decode() if msg else ""))
-        return outputs, [x.as_dict() for x in i1], [x.as_dict() for x in i2]
+        return (outputs, [x.as_dict(len(m.shapes)) for x, m in zip(i1, self.members)],
+                [x.as_dict(len(m.shapes)) for x, m in zip(i2, self.members)])
 
     def close(self):
         if getattr(self, "b", None):

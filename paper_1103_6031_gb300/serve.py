@@ -298,7 +298,8 @@ class NativeServer:
                     req, out, _, _ = self.inflight.pop(r.id)
                     req.admitted = r.t_start if self._clock_ok else None
                     req.done = r.t_done if self._clock_ok else now
-                    req.info = (r.info1.as_dict(), r.info2.as_dict())
+                    nl = req.cfg.n_levels
+                    req.info = (r.info1.as_dict(nl), r.info2.as_dict(nl))
                     if r.status != 0:
                         req.error = mg.MGError(r.status, "request %d: %s"
                                                % (req.id, r.error.decode(errors="replace")))

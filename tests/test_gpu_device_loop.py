@@ -57,6 +57,7 @@ def _same_info(a, b):
     assert a["rel_residual"] == b["rel_residual"]
     assert a["source_mean"] == b["source_mean"]
     assert a["history"] == b["history"]
+    assert a["level_rel_residual"] == b["level_rel_residual"]
 
 
 @pytest.mark.parametrize("name,geom,mixed", CASES, ids=[c[0] for c in CASES])

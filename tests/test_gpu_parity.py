@@ -92,6 +92,11 @@ def test_nested_pipeline_matched_cycles(lib, geom):
     assert i1["cycles"] == cycles and i2["cycles"] == cycles
     np.testing.assert_allclose(i1["history"], ref["info1"]["history"], rtol=1e-6, atol=1e-14)
     np.testing.assert_allclose(i2["history"], ref["info2"]["history"], rtol=1e-6, atol=1e-14)
+    # per-level relative residuals of the last cycle (Sec. 3.2 norm, level by level)
+    np.testing.assert_allclose(i1["level_rel_residual"], ref["info1"]["level_rel_residual"],
+                               rtol=1e-6, atol=1e-14)
+    np.testing.assert_allclose(i2["level_rel_residual"], ref["info2"]["level_rel_residual"],
+                               rtol=1e-6, atol=1e-14)
     for l in range(geom.n_levels):
         assert rel(out["phi1"][l], ref["phi1"][l]) < TOL
         assert rel(out["phi2"][l], ref["phi2"][l]) < TOL

@@ -382,3 +382,31 @@ def test_edge_ghosts_exact_on_tensor_linear_field(order, noncubic):
     X, Y, Z = _centres(lev, origin, extra=lev.g)
     expect = _tensor_linear(X, Y, Z)
     np.testing.assert_allclose(lev.u, expect, atol=1e-12)
+
+
+def test_per_level_residual_norms_add_up_to_the_leaf_norm():
+    """The per-level sums of the leaf residual norm (reading of the Sec. 3.2 stopping
+    rule, level by level) add up to the composite norm, and a residual that lives on
+    one level's leaf cells shows up on that level only."""
+    from oracle.multigrid import level_relative_residuals
+    geom = small_zoom(24, ((20, 7), (16, 6)), order=4, box=50.0)
+    hier = Hierarchy(geom)
+    rng = np.random.default_rng(4)
+    for l in hier.leaf_levels():
+        hier.levels[l].f[...] = rng.standard_normal(hier.levels[l].n)
+        hier.levels[l].interior[...] = rng.standard_normal(hier.levels[l].n)
+    pairs = []
+    rn, fn = leaf_residual_norms(hier, per_level=pairs)
+    assert len(pairs) == 3
+    assert abs(np.sqrt(sum(p[0] for p in pairs)) - rn) < 1e-13 * rn
+    assert abs(np.sqrt(sum(p[1] for p in pairs)) - fn) < 1e-13 * fn
+    # u = 0 and a source on the finest level only: relative residual 1 there, 0 elsewhere
+    for l in hier.leaf_levels():
+        hier.levels[l].u[...] = 0.0
+        hier.levels[l].f[...] = 0.0
+    hier.levels[hier.finest].f[...] = 1.0
+    pairs = []
+    leaf_residual_norms(hier, per_level=pairs)
+    rel = level_relative_residuals(pairs)
+    assert rel[0] == 0.0 and rel[1] == 0.0
+    assert abs(rel[2] - 1.0) < 1e-14

@@ -222,8 +222,10 @@ mg_status mg_lpt_pipeline(mg_hierarchy* h, int host_buffers, const double* const
  * Working memory is one static device array of 16 MiB (five ghost-padded grids,
  * about 64^3 cells at order 6); larger grids return MG_EINVAL with a message.
  * The first call on each device looks up the array's address and should be
- * made outside stream capture.  Calls share the array: calls whose work
- * overlaps on the GPU race.  Asynchronous on cuda_stream. */
+ * made outside stream capture; the address is kept until the process exits, so
+ * the call must not be used on a device after cudaDeviceReset in the same
+ * process.  Calls share the array: calls whose work overlaps on the GPU race,
+ * so callers serialise them.  Asynchronous on cuda_stream. */
 mg_status mg_lpt2_source_periodic_static(const double* phi, double* tau, int n0, int n1,
                                          int n2, double box, int order, void* cuda_stream,
                                          char* err, size_t len);

@@ -12,7 +12,10 @@
 //
 // The device address of the array is looked up once per device, on the first
 // call made while that device is current (cudaGetSymbolAddress); make that
-// first call outside any stream capture.  All calls share the array and each
+// first call outside any stream capture.  The address is kept until the process
+// exits: after cudaDeviceReset the module is loaded again, possibly elsewhere, so
+// this entry point must not be called on a device that was reset in the same
+// process.  All calls share the array and each
 // call overwrites every element it later reads, so nothing carries over from
 // a previous call; two calls whose work overlaps on the GPU (different
 // streams, or different host threads) race on the array.

@@ -381,6 +381,14 @@ const char* mg_last_error(const mg_hierarchy* h);
  * device memory on the current device; the CUDA context stays usable. */
 mg_status mg_selftest_wait_limit(void);
 
+/* Measured issue rate of the FP64 pipe of the current device, the roofline
+ * denominator of the float64 stencil kernels (no counterpart in the paper): one
+ * warm-up launch, then one timed launch of 8 blocks of 256 threads per SM, each
+ * thread running 8 independent chains of `iters` fused multiply-adds (16 <= iters
+ * <= 2^22; 4096 takes about 20 ms on a GB300).  *fma_per_s = FP64 FMAs per second.
+ * Synchronous on cuda_stream; allocates nothing.  Errors: MG_EINVAL, MG_ECUDA. */
+mg_status mg_fp64_fma_rate(int iters, void* cuda_stream, double* fma_per_s);
+
 /* ---- Density generator (Hahn & Abel 2011, Sec. 2.1) ----------------------------
  * Gaussian white noise from a counter-based generator and its periodic
  * convolution with a radial amplitude: delta = IFFT[A(|k|) FFT[noise]], the

@@ -18,7 +18,9 @@
 //
 // Every wait on an mbarrier is bounded (kWaitNs of global time); a block whose
 // wait ran out sets *err, stops, drains its copies in flight (again bounded) and
-// returns, so a lost copy surfaces as an error status instead of a hang.
+// returns, so a lost copy surfaces as an error status instead of a hang.  Blocks
+// that are still waiting give up as soon as *err is set (and later launches on the
+// same flag fail fast), so the whole launch ends within about one wait limit.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -91,12 +93,18 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// true once the phase with this parity has completed; false after kWaitNs
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+// true once the phase with this parity has completed; false after kWaitNs, or as
+// soon as *stop is non-zero (another block of the launch gave up already, so a lost
+// copy surfaces after about one wait limit rather than one per block wave); stop may
+// be null (the drain of a failing block waits for its own copies regardless)
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity,
+                                          const unsigned* stop) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
-  while (!mbar_try_wait(bar, parity))
+  while (!mbar_try_wait(bar, parity)) {
     if (global_ns() - t0 > kWaitNs) return false;
+    if (stop && *reinterpret_cast<const volatile unsigned*>(stop) != 0u) return false;
+  }
   return true;
 }
 
@@ -177,7 +185,7 @@ __global__ void __launch_bounds__(32 * kTY)
   V2 q[NT];  // q[t]: this thread's pair in staged plane t
 #pragma unroll
   for (int t = 0; t < 2 * H; ++t) {
-    bad |= !mbar_wait(&bar[t % kSlots], (t / kSlots) & 1);
+    bad |= !mbar_wait(&bar[t % kSlots], (t / kSlots) & 1, err);
     q[t] = *reinterpret_cast<const V2*>(tiles + (t % kSlots) * TL::stride + own);
   }
   waited = 2 * H;
@@ -198,7 +206,7 @@ __global__ void __launch_bounds__(32 * kTY)
     for (int s = 0; s < kLX; ++s) {
       if (s < nu) {
         const int tq = s + 2 * H;  // plane entering the queue
-        bad |= !mbar_wait(&bar[tq % kSlots], (tq / kSlots) & 1);
+        bad |= !mbar_wait(&bar[tq % kSlots], (tq / kSlots) & 1, err);
         q[tq] = *reinterpret_cast<const V2*>(tiles + (tq % kSlots) * TL::stride + own);
         waited = tq + 1;
         if (active) {
@@ -263,7 +271,7 @@ __global__ void __launch_bounds__(32 * kTY)
 fail:
   // drain the copies this block issued and has not waited for, then report
   if (issuer) {
-    for (int t = waited; t < next; ++t) mbar_wait(&bar[t % kSlots], (t / kSlots) & 1);
+    for (int t = waited; t < next; ++t) mbar_wait(&bar[t % kSlots], (t / kSlots) & 1, nullptr);
     atomicOr(err, 1u);
   }
 }

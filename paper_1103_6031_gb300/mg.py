@@ -165,6 +165,7 @@ def load_library(path=None):
         "mg_batch_last_error": (ctypes.c_char_p, [vp]),
         "mg_last_error": (ctypes.c_char_p, [vp]),
         "mg_selftest_wait_limit": (ctypes.c_int, []),
+        "mg_fp64_fma_rate": (ctypes.c_int, [ctypes.c_int, vp, ctypes.POINTER(ctypes.c_double)]),
         "mg_hybrid_correction": (ctypes.c_int, [vp, vp, ctypes.POINTER(vp)]),
         "mg_lla_density": (ctypes.c_int, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_double,
                                           ctypes.c_double, ctypes.POINTER(vp)]),
@@ -477,6 +478,17 @@ def selftest_wait_limit():
     """Runs the device wait-limit self-test (about 2 s); returns the status name,
     "MG_ETIMEOUT" when the bounded wait and its error path work."""
     return STATUS.get(int(load_library().mg_selftest_wait_limit()), "unknown")
+
+
+def fp64_fma_rate(iters=4096, stream=None):
+    """FP64 fused multiply-adds per second the current device issues
+    (mg_fp64_fma_rate): the measured denominator of the float64 stencils' roofline."""
+    out = ctypes.c_double(0.0)
+    sp = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+    st = load_library().mg_fp64_fma_rate(int(iters), sp, ctypes.byref(out))
+    if st != 0:
+        raise MGError(st, "mg_fp64_fma_rate")
+    return out.value
 
 
 def _dense_f64(t, name):

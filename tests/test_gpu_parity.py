@@ -194,23 +194,6 @@ def test_errors_are_reported(lib):
     assert st == 1
 
 
-def test_bench_tolerance_gives_1e6_error(lib):
-    """The benchmark stops each solve at a relative leaf residual of 1e-7; on its
-    workload that leaves <= 1e-6 RMS relative error in phi1, phi2 and both
-    displacement fields against tightly converged solves (1e-12)."""
-    import bench
-    geom = config_zoom2()
-    deltas = to_dev(make_delta(geom, bench.SEED))
-    loose = hier(lib, geom, tol=bench.SOLVE_TOL)
-    tight = hier(lib, geom, tol=1e-12)
-    a, i1, i2 = loose.pipeline(deltas)
-    b, _, _ = tight.pipeline(deltas)
-    for key in ("phi1", "phi2", "disp1", "disp2"):
-        for x, y in zip(a[key], b[key]):
-            assert rel(x, y.cpu().numpy()) <= 1e-6, key
-    assert i1["cycles"] + i2["cycles"] == bench.CYCLES_PER_STEP["zoom2"]
-
-
 @pytest.mark.parametrize("order", (2, 4, 6))
 def test_mixed_precision_matches_fp64_oracle(lib, order):
     """MG_MIXED (float32 V-cycles inside float64 iterative refinement) reaches the
@@ -232,26 +215,11 @@ def test_mixed_precision_matches_fp64_oracle(lib, order):
             assert rel(out["disp2"][3 * l + a], ref["psi2"][l][a]) <= 1e-6
 
 
-def test_mixed_precision_bench_workload(lib):
-    """On the benchmark workload at its stopping tolerance the mixed-precision step
-    stays within 1e-6 RMS relative error of tightly converged float64 solves."""
-    import bench
-    geom = config_zoom2()
-    deltas = to_dev(make_delta(geom, bench.SEED))
-    mixed = hier(lib, geom, tol=bench.SOLVE_TOL, precision=lib.MG_MIXED,
-                 inner_cycles=bench.MIXED_INNER_CYCLES)
-    tight = hier(lib, geom, tol=1e-12)
-    a, i1, i2 = mixed.pipeline(deltas)
-    b, _, _ = tight.pipeline(deltas)
-    for key in ("phi1", "phi2", "disp1", "disp2"):
-        for x, y in zip(a[key], b[key]):
-            assert rel(x, y.cpu().numpy()) <= 1e-6, key
-
-
 def test_deep_zoom_full_size(lib):
     """128^3 base + 4 nests of 128^3 (jittered offsets): float64 matches the oracle
-    element by element at a matched cycle count; the mixed-precision step stays
-    within 1e-6 of tightly converged float64 solves."""
+    element by element at a matched cycle count, and converges at >= 10x per cycle
+    down to the rounding floor (the mixed-precision step against the converged oracle
+    is in test_gpu_full_size_oracle.py)."""
     from synthetic import config_deep_zoom
     geom = config_deep_zoom()
     deltas = make_delta(geom, 3)
@@ -268,11 +236,6 @@ def test_deep_zoom_full_size(lib):
     hist = t1["history"]
     # >= 10x per cycle until the float64 rounding floor of the composite residual
     assert all(x / y >= 10.0 for x, y in zip(hist[:-1], hist[1:]) if y > 1e-10), hist
-    mixed = hier(lib, geom, tol=1e-7, precision=lib.MG_MIXED, inner_cycles=4)
-    a, _, _ = mixed.pipeline(d)
-    for key in ("phi1", "phi2", "disp1", "disp2"):
-        for x, y in zip(a[key], b[key]):
-            assert rel(x, y.cpu().numpy()) <= 1e-6, key
 
 
 @pytest.mark.parametrize("mixed", [False, True], ids=["fp64", "mixed"])

@@ -62,6 +62,32 @@ __global__ void __launch_bounds__(256) k_ghost_periodic(Grid G, T* __restrict__ 
   u[gidx(G, i, j, k)] = u[gidx(G, si, sj, sk)];
 }
 
+// The interpolation and flux weights in the kernels' own precision.  The host
+// rounds the float64 weights once (round to nearest, the rounding of the device's
+// T(double) conversion), so results are bit-identical to converting each weight on
+// the device, without the per-use conversions (double to float conversions issue on
+// the FP64 pipe, which bounded the float32 ghost kernels).
+template <typename T>
+struct CfW {
+  T tang[2][7];
+  T ncoarse[3][3];
+  T nfine[3][4];
+  T flux[6];
+};
+
+template <typename T>
+CfW<T> cf_weights_as(const CfWeights& w) {
+  CfW<T> o;
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 7; ++b) o.tang[a][b] = T(w.tang[a][b]);
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) o.ncoarse[a][b] = T(w.ncoarse[a][b]);
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 4; ++b) o.nfine[a][b] = T(w.nfine[a][b]);
+  for (int a = 0; a < 6; ++a) o.flux[a] = T(w.flux[a]);
+  return o;
+}
+
 __device__ __forceinline__ void face_axes(int a, int& b, int& c) {
   b = (a == 0) ? 1 : 0;
   c = (a == 2) ? 1 : 2;
@@ -82,7 +108,7 @@ __device__ __forceinline__ int face_of(const FaceSet& fs, long long t, const lon
 // as the per-position form: a quarter of the loads, ~0.56 of the float64 work).
 template <int ORDER, typename T>
 __global__ void __launch_bounds__(128)
-    k_cf_tangential(Grid F, Grid P, const T* __restrict__ pu, Int3 off, FaceSet fs, CfWeights w,
+    k_cf_tangential(Grid F, Grid P, const T* __restrict__ pu, Int3 off, FaceSet fs, CfW<T> w,
                     T invH, T* __restrict__ inter, T* __restrict__ fc_unc) {
   constexpr int half = ORDER / 2;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -119,8 +145,8 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
     for (int cc = 0; cc <= ORDER; ++cc) {
       const T v = __ldg(pu + p0 + bb * sb + cc * sc);
-      r0 = fma(T(w.tang[0][cc]), v, r0);
-      r1 = fma(T(w.tang[1][cc]), v, r1);
+      r0 = fma(w.tang[0][cc], v, r0);
+      r1 = fma(w.tang[1][cc], v, r1);
     }
     row[0][bb] = r0;
     row[1][bb] = r1;
@@ -131,8 +157,8 @@ __global__ void __launch_bounds__(128)
     T acc0 = T(0), acc1 = T(0);
 #pragma unroll
     for (int bb = 0; bb <= ORDER; ++bb) {
-      acc0 = fma(T(w.tang[pj][bb]), row[0][bb], acc0);
-      acc1 = fma(T(w.tang[pj][bb]), row[1][bb], acc1);
+      acc0 = fma(w.tang[pj][bb], row[0][bb], acc0);
+      acc1 = fma(w.tang[pj][bb], row[1][bb], acc1);
     }
     // (tk, tk + 1) = (2 kc, 2 kc + 1): an even, hence 2-element aligned, pair
     V2 out;
@@ -148,7 +174,7 @@ __global__ void __launch_bounds__(128)
     const long long q0 = p0 + half * sb + half * sc + (long long)(pface - half - pn) * sa;
     T fc = T(0);
     const int s0 = side == 0 ? 0 : half, s1 = side == 0 ? half : ORDER;
-    for (int s = s0; s < s1; ++s) fc = fma(T(w.flux[s]), __ldg(pu + q0 + s * sa), fc);
+    for (int s = s0; s < s1; ++s) fc = fma(w.flux[s], __ldg(pu + q0 + s * sa), fc);
     fc_unc[fs.ebase[f] + (long long)jc * ne1 + kc] = fc * invH;
   }
 }
@@ -163,7 +189,7 @@ __global__ void __launch_bounds__(128)
 // the flux weights on the ghost side).
 template <int ORDER, typename T>
 __global__ void __launch_bounds__(128)
-    k_cf_flux(Grid F, T* __restrict__ u, FaceSet fs, CfWeights w, const T* __restrict__ inter,
+    k_cf_flux(Grid F, T* __restrict__ u, FaceSet fs, CfW<T> w, const T* __restrict__ inter,
               const T* __restrict__ fc_unc, T fc_scale, T a0, T a1, T b0, T b1, int flux_fix) {
   constexpr int half = ORDER / 2;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -200,7 +226,7 @@ __global__ void __launch_bounds__(128)
     T pair = u[in0 + (2 * d) * step] + u[in0 + (2 * d + 1) * step];
     pair += __shfl_xor_sync(quad, pair, 1);
     pair += __shfl_xor_sync(quad, pair, 2);
-    cov = fma(T(w.flux[s]), pair, cov);
+    cov = fma(w.flux[s], pair, cov);
   }
   const T fc = fma(cov, fc_scale, fc_unc[e]);
   T cq[half];
@@ -211,9 +237,9 @@ __global__ void __launch_bounds__(128)
   for (int m = 0; m < half; ++m) {
     T gv = T(0);
 #pragma unroll
-    for (int q = 0; q < half; ++q) gv = fma(T(w.ncoarse[m][q]), cq[q], gv);
+    for (int q = 0; q < half; ++q) gv = fma(w.ncoarse[m][q], cq[q], gv);
 #pragma unroll
-    for (int q = 0; q <= half; ++q) gv = fma(T(w.nfine[m][q]), v[q], gv);
+    for (int q = 0; q <= half; ++q) gv = fma(w.nfine[m][q], v[q], gv);
     ghost[m] = gv;
   }
   T ff = T(0);
@@ -222,7 +248,7 @@ __global__ void __launch_bounds__(128)
     T x;
     if (side == 0) x = s < half ? ghost[half - 1 - s] : v[s - half];
     else x = s < half ? v[half - 1 - s] : ghost[s - half];
-    ff = fma(T(w.flux[s]), x, ff);
+    ff = fma(w.flux[s], x, ff);
   }
   ff += __shfl_xor_sync(quad, ff, 1);
   ff += __shfl_xor_sync(quad, ff, 2);
@@ -282,10 +308,11 @@ cudaError_t launch_cf_tangential(int order, const Grid& F, const Grid& P, const 
                                  T* fc_unc, cudaStream_t s) {
   const int block = 128;
   const unsigned grid = (unsigned)(((order / 2) * fs.ebase[6] + block - 1) / block);
+  const CfW<T> wt = cf_weights_as<T>(w);
   switch (order) {
-    case 2: k_cf_tangential<2, T><<<grid, block, 0, s>>>(F, P, pu, off, fs, w, T(invH), inter, fc_unc); break;
-    case 4: k_cf_tangential<4, T><<<grid, block, 0, s>>>(F, P, pu, off, fs, w, T(invH), inter, fc_unc); break;
-    case 6: k_cf_tangential<6, T><<<grid, block, 0, s>>>(F, P, pu, off, fs, w, T(invH), inter, fc_unc); break;
+    case 2: k_cf_tangential<2, T><<<grid, block, 0, s>>>(F, P, pu, off, fs, wt, T(invH), inter, fc_unc); break;
+    case 4: k_cf_tangential<4, T><<<grid, block, 0, s>>>(F, P, pu, off, fs, wt, T(invH), inter, fc_unc); break;
+    case 6: k_cf_tangential<6, T><<<grid, block, 0, s>>>(F, P, pu, off, fs, wt, T(invH), inter, fc_unc); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -300,10 +327,11 @@ cudaError_t launch_cf_flux(int order, const Grid& F, T* u, const FaceSet& fs, co
   const T fc_scale = T(0.125 * invH);
   const T a0 = T(h / w.ghost_coef[0]), a1 = T(h / w.ghost_coef[1]);
   const T b0 = T(0.25 * invh * h / w.ghost_coef[0]), b1 = T(0.25 * invh * h / w.ghost_coef[1]);
+  const CfW<T> wt = cf_weights_as<T>(w);
   switch (order) {
-    case 2: k_cf_flux<2, T><<<grid, block, 0, s>>>(F, u, fs, w, inter, fc_unc, fc_scale, a0, a1, b0, b1, flux_fix); break;
-    case 4: k_cf_flux<4, T><<<grid, block, 0, s>>>(F, u, fs, w, inter, fc_unc, fc_scale, a0, a1, b0, b1, flux_fix); break;
-    case 6: k_cf_flux<6, T><<<grid, block, 0, s>>>(F, u, fs, w, inter, fc_unc, fc_scale, a0, a1, b0, b1, flux_fix); break;
+    case 2: k_cf_flux<2, T><<<grid, block, 0, s>>>(F, u, fs, wt, inter, fc_unc, fc_scale, a0, a1, b0, b1, flux_fix); break;
+    case 4: k_cf_flux<4, T><<<grid, block, 0, s>>>(F, u, fs, wt, inter, fc_unc, fc_scale, a0, a1, b0, b1, flux_fix); break;
+    case 6: k_cf_flux<6, T><<<grid, block, 0, s>>>(F, u, fs, wt, inter, fc_unc, fc_scale, a0, a1, b0, b1, flux_fix); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

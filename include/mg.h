@@ -90,6 +90,15 @@ typedef enum { MG_FP64 = 0, MG_MIXED = 1 } mg_precision;
  * host loop, so no host round trip separates two iterations.  Same launches and
  * results as the host loop; ignored with MG_FLAG_NO_GRAPHS or while profiling. */
 #define MG_FLAG_DEVICE_LOOP 16
+/* MG_FLAG_PERSISTENT: in mg_batch_lpt_pipeline, when every member is MG_MIXED and sets
+ * this flag, the float32 half of each outer iteration of all active members (zero
+ * correction, inner V-cycles) runs as ONE persistent kernel launch over a work list of
+ * (hierarchy, level operation, block range) items, instead of one launch per level
+ * operation per member: blocks take items in chain order and wait, bounded by 2 s, for
+ * their hierarchy's earlier operations (a wait that runs out gives MG_ETIMEOUT).  The
+ * float64 half (update, ghosts, residual norm) follows on the members' own streams.
+ * Results are bit-identical to the per-operation launches.  Ignored outside a batch. */
+#define MG_FLAG_PERSISTENT 32
 
 typedef struct {
   int n_levels;                        /* 1 = base only; 1 + number of nests            */
@@ -388,6 +397,14 @@ mg_status mg_selftest_wait_limit(void);
  * <= 2^22; 4096 takes about 20 ms on a GB300).  *fma_per_s = FP64 FMAs per second.
  * Synchronous on cuda_stream; allocates nothing.  Errors: MG_EINVAL, MG_ECUDA. */
 mg_status mg_fp64_fma_rate(int iters, void* cuda_stream, double* fma_per_s);
+
+/* Self-test of the persistent batch kernel's bounded dependency wait (no counterpart
+ * in the paper): one launch of that kernel on an internal two-item work list whose
+ * second item depends on an operation that does not exist, with a 100 ms wait limit.
+ * Returns MG_ETIMEOUT when the limit and the error path work, MG_OK if the wait did
+ * not give up (a defect), MG_ENOMEM or MG_ECUDA on a CUDA failure.  Synchronous;
+ * allocates and frees its own device memory; the CUDA context stays usable. */
+mg_status mg_selftest_persist_wait(void);
 
 /* ---- Density generator (Hahn & Abel 2011, Sec. 2.1) ----------------------------
  * Gaussian white noise from a counter-based generator and its periodic

@@ -16,16 +16,19 @@
 // the same composite operator), and adds e to u in float64.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cfloat>
 #include <cstdio>
 #include <cstring>
 #include <map>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "mg.h"
 #include "mg_internal.h"
+#include "mg_persist.h"
 #include "mg_setup.h"
 
 using namespace mgk;
@@ -243,6 +246,10 @@ struct mg_hierarchy {
   int inner_now = 0;  // MG_MIXED: float32 V-cycles of the next outer iteration
   Graph* capturing = nullptr;     // graph being captured
   Graph* replayed = nullptr;      // graph whose event pairs await reading
+  // when set, the float32 level operations are appended here (a work list for the
+  // persistent batch kernel) instead of being launched; the host-side state (buffer
+  // parities, stale flags) advances exactly as for launches
+  std::vector<mgk::POp>* rec = nullptr;
   CfWeights w;
   std::string err;
   void* arena = nullptr;
@@ -360,6 +367,34 @@ mg_status prof_end(mg_hierarchy* h, int fam, long long cells) {
   } while (0)
 
 long long cells_of(const Grid& G) { return (long long)G.n0 * G.n1 * G.n2; }
+
+// ---- work-list recording (persistent batch kernel) -----------------------------
+
+template <typename T>
+bool recording(const mg_hierarchy* h) {
+  return std::is_same<T, float>::value && h->rec != nullptr;
+}
+
+// Appends an operation of nblk blocks; 3D operations give their grid's x and y extents.
+void rec_push(mg_hierarchy* h, POp op, long long nblk, int gx = 1, int gy = 1) {
+  op.nblk = (int)nblk;
+  op.gx = gx;
+  op.gy = gy;
+  // about 1024 work items per operation at most: few atomics, enough items to spread
+  op.per_tile = (int)(nblk > 1024 ? (nblk + 1023) / 1024 : 1);
+  op.ntiles = (int)((nblk + op.per_tile - 1) / op.per_tile);
+  op.order = h->cfg.order;
+  if (nblk > 0) h->rec->push_back(op);
+}
+
+POp pop(int kind) {
+  POp o;
+  std::memset(&o, 0, sizeof(o));
+  o.kind = kind;
+  return o;
+}
+
+long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
 long long cells_of(Int3 c) { return (long long)c.x * c.y * c.z; }
 long long shell_of(const Grid& G) {
   return (long long)G.X * G.Y * (G.n2 + 2 * G.g) - cells_of(G);
@@ -575,6 +610,19 @@ mg_status tangential(mg_hierarchy* h, int l) {
   DevLevel& P = h->L[l - 1];
   Bufs<T>& b = bufs<T>(L);
   Bufs<T>& pb = bufs<T>(P);
+  if (recording<T>(h)) {
+    POp o = pop(P_TANG);
+    o.F = L.G;
+    o.P = P.G;
+    o.in0 = reinterpret_cast<const float*>(pb.u[pb.cur]);
+    o.off = L.off;
+    o.fs = L.fs;
+    o.s[0] = float(1.0 / P.geo.h);
+    o.out0 = reinterpret_cast<float*>(b.inter);
+    o.out1 = reinterpret_cast<float*>(b.fc_unc);
+    rec_push(h, o, ceil_div((h->cfg.order / 2) * L.fs.ebase[6], kPersistThreads));
+    return MG_OK;
+  }
   KL(MG_K_GHOST, L.fs.base[6],
      launch_cf_tangential<T>(h->cfg.order, L.G, P.G, pb.u[pb.cur], L.off, L.fs, h->w,
                              1.0 / P.geo.h, b.inter, b.fc_unc, h->s));
@@ -586,13 +634,38 @@ mg_status ghost_fill(mg_hierarchy* h, int l, bool edges) {
   DevLevel& L = h->L[l];
   Bufs<T>& b = bufs<T>(L);
   if (L.periodic) {
-    if (b.ghosts_stale)
-      KL(MG_K_GHOST, shell_of(L.G), launch_ghost_periodic<T>(L.G, b.u[b.cur], h->s));
+    if (b.ghosts_stale) {
+      if (recording<T>(h)) {
+        POp o = pop(P_GHOST_PERIODIC);
+        o.F = L.G;
+        o.out0 = reinterpret_cast<float*>(b.u[b.cur]);
+        rec_push(h, o, ceil_div(ghost_shell_count(L.G), kPersistThreads));
+      } else {
+        KL(MG_K_GHOST, shell_of(L.G), launch_ghost_periodic<T>(L.G, b.u[b.cur], h->s));
+      }
+    }
     b.ghosts_stale = false;
     return MG_OK;
   }
   DevLevel& P = h->L[l - 1];
   Bufs<T>& pb = bufs<T>(P);
+  if (recording<T>(h) && !edges) {
+    // the scale factors exactly as launch_cf_flux rounds them
+    const double hh = L.geo.h, invh = 1.0 / L.geo.h, invH = 1.0 / P.geo.h;
+    POp o = pop(P_CF_FLUX);
+    o.F = L.G;
+    o.out0 = reinterpret_cast<float*>(b.u[b.cur]);
+    o.fs = L.fs;
+    o.in0 = reinterpret_cast<const float*>(b.inter);
+    o.in1 = reinterpret_cast<const float*>(b.fc_unc);
+    o.s[0] = float(0.125 * invH);
+    o.s[1] = float(hh / h->w.ghost_coef[0]);
+    o.s[2] = float(hh / h->w.ghost_coef[1]);
+    o.s[3] = float(0.25 * invh * hh / h->w.ghost_coef[0]);
+    o.s[4] = float(0.25 * invh * hh / h->w.ghost_coef[1]);
+    rec_push(h, o, ceil_div(4 * L.fs.ebase[6], kPersistThreads));
+    return MG_OK;
+  }
   KL(MG_K_GHOST, 4 * L.fs.ebase[6] * L.G.g,
      launch_cf_flux<T>(h->cfg.order, L.G, b.u[b.cur], L.fs, h->w, b.inter, b.fc_unc, L.geo.h,
                        1.0 / L.geo.h, 1.0 / P.geo.h, 1, h->s));
@@ -608,6 +681,22 @@ mg_status half_sweep(mg_hierarchy* h, int l, int colour) {
   Bufs<T>& b = bufs<T>(L);
   ST(ghost_fill<T>(h, l, false));
   const double a_f = L.geo.h * L.geo.h / centre_weight(h->cfg.order);
+  if (recording<T>(h)) {
+    // the plain smoother's arithmetic (bit-identical to the TMA-staged one), 32 x 4
+    // threads per block
+    POp o = pop(P_SMOOTH);
+    o.F = L.G;
+    o.in0 = reinterpret_cast<const float*>(b.u[b.cur]);
+    o.out0 = reinterpret_cast<float*>(b.u[1 - b.cur]);
+    o.in1 = reinterpret_cast<const float*>(b.ffas);
+    o.s[0] = float(a_f);
+    o.colour = colour;
+    o.periodic = L.periodic ? 1 : 0;
+    const long long gx = ceil_div((L.G.n2 + 1) / 2, 32), gy = ceil_div(L.G.n1, 4);
+    rec_push(h, o, gx * gy * L.G.n0, (int)gx, (int)gy);
+    b.cur ^= 1;
+    return MG_OK;
+  }
   if (b.tma)
     KL(MG_K_SMOOTH, (cells_of(L.G) + 1) / 2,
        launch_smooth_half_tma<T>(h->cfg.order, L.G, &b.tm[b.cur], &b.tm_f, b.u[1 - b.cur], a_f,
@@ -636,6 +725,15 @@ mg_status vcycle(mg_hierarchy* h, int l) {
   Bufs<T>& b = bufs<T>(L);
   const int order = h->cfg.order;
   if (l == 0) {
+    if (recording<T>(h)) {
+      POp o = pop(P_COARSEST);
+      o.F = L.G;
+      o.in0 = reinterpret_cast<const float*>(b.ffas);
+      o.out0 = reinterpret_cast<float*>(b.u[b.cur]);
+      o.kern = L.kern;
+      rec_push(h, o, cells_of(L.G));
+      return MG_OK;
+    }
     KL(MG_K_COARSEST, cells_of(L.G), launch_coarsest(L.G, b.ffas, b.u[b.cur], L.kern, h->s));
     return MG_OK;
   }
@@ -643,6 +741,45 @@ mg_status vcycle(mg_hierarchy* h, int l) {
   Bufs<T>& pb = bufs<T>(P);
   ST(smooth<T>(h, l, h->cfg.nu1));
   ST(ghost_fill<T>(h, l, false));
+  if (recording<T>(h)) {
+    const long long gx = ceil_div(L.cn.z, 32), gy = ceil_div(L.cn.y, 4);
+    POp o = pop(P_RESTRICT);
+    o.F = L.G;
+    o.P = P.G;
+    o.in0 = reinterpret_cast<const float*>(b.u[b.cur]);
+    o.in1 = reinterpret_cast<const float*>(b.ffas);
+    o.s[0] = float(1.0 / (L.geo.h * L.geo.h));
+    o.out0 = reinterpret_cast<float*>(pb.u[pb.cur]);
+    o.out1 = reinterpret_cast<float*>(pb.ffas);
+    o.out2 = reinterpret_cast<float*>(b.ubar);
+    o.off = L.off;
+    o.cn = L.cn;
+    o.periodic = P.periodic ? 1 : 0;
+    rec_push(h, o, gx * gy * L.cn.x, (int)gx, (int)gy);
+    POp q = pop(P_FAS);
+    q.P = P.G;
+    q.in0 = reinterpret_cast<const float*>(pb.u[pb.cur]);
+    q.out0 = reinterpret_cast<float*>(pb.ffas);
+    q.s[0] = float(1.0 / (P.geo.h * P.geo.h));
+    q.off = L.off;
+    q.cn = L.cn;
+    rec_push(h, q, gx * gy * L.cn.x, (int)gx, (int)gy);
+    ST(vcycle<T>(h, l - 1));
+    if (!L.periodic) ST(tangential<T>(h, l));
+    const long long px = ceil_div(L.G.n2 / 2, 32), py = ceil_div(L.G.n1, 4);
+    POp r = pop(P_PROLONG);
+    r.F = L.G;
+    r.out0 = reinterpret_cast<float*>(b.u[b.cur]);
+    r.P = P.G;
+    r.in0 = reinterpret_cast<const float*>(pb.u[pb.cur]);
+    r.in1 = reinterpret_cast<const float*>(b.ubar);
+    r.off = L.off;
+    r.cn = L.cn;
+    r.periodic = L.periodic ? 1 : 0;
+    rec_push(h, r, px * py * L.G.n0, (int)px, (int)py);
+    ST(smooth<T>(h, l, h->cfg.nu2));
+    return MG_OK;
+  }
   KL(MG_K_RESTRICT, cells_of(L.G),
      launch_residual_restrict<T>(order, L.G, b.u[b.cur], b.ffas, 1.0 / (L.geo.h * L.geo.h), P.G,
                                  pb.u[pb.cur], pb.ffas, b.ubar, L.off, L.cn,
@@ -745,7 +882,8 @@ mg_status norm_read(mg_hierarchy* h, double* rr, double* ff, double* fsum) {
   std::memcpy(&flag, h->host_red + 4, sizeof(flag));
   if (flag)
     return fail(h, MG_ETIMEOUT,
-                "a smoother block's wait for a staged plane tile ran out; outputs are invalid");
+                "a bounded device-side wait ran out (a smoother block's wait for a staged plane "
+                "tile, or a persistent batch item's wait for its dependency); outputs are invalid");
   *rr = h->host_red[0];
   *ff = h->host_red[1];
   if (fsum) *fsum = h->host_red[2];
@@ -830,22 +968,40 @@ mg_status fp64_cycle_body(mg_hierarchy* h) {
 // the other buffer before it is read), and a zero parent gives zero
 // tangential intermediate values and parent fluxes on every nest.
 mg_status zero_correction(mg_hierarchy* h) {
+  auto zero = [&](float* p, long long n) -> mg_status {
+    if (h->rec) {
+      POp o = pop(P_ZERO);
+      o.out0 = p;
+      o.n = n;
+      rec_push(h, o, ceil_div(n, kZeroPerBlock));
+      return MG_OK;
+    }
+    CK(cudaMemsetAsync(p, 0, (size_t)n * sizeof(float), h->s));
+    return MG_OK;
+  };
   for (int l = 0; l <= finest(h); ++l) {
     DevLevel& L = h->L[l];
     L.s.cur = 0;
     L.s.ghosts_stale = false;
-    CK(cudaMemsetAsync(L.s.u[0], 0, (size_t)grid_elems(L.G) * sizeof(float), h->s));
+    ST(zero(L.s.u[0], grid_elems(L.G)));
     if (L.geo.nest) {
-      CK(cudaMemsetAsync(L.s.inter, 0, (size_t)L.fs.base[6] * sizeof(float), h->s));
-      CK(cudaMemsetAsync(L.s.fc_unc, 0, (size_t)L.fs.ebase[6] * sizeof(float), h->s));
+      ST(zero(L.s.inter, L.fs.base[6]));
+      ST(zero(L.s.fc_unc, L.fs.ebase[6]));
     }
   }
   return MG_OK;
 }
 
-mg_status mixed_outer_body(mg_hierarchy* h) {
+// The float32 half of an outer iteration: zero correction, inner_now V-cycles.
+mg_status mixed_inner(mg_hierarchy* h) {
   ST(zero_correction(h));
   for (int m = 0; m < h->inner_now; ++m) ST(vcycle<float>(h, finest(h)));
+  return MG_OK;
+}
+
+// The float64 half: u += e on the leaf levels, the solution's tangential ghosts, the
+// leaf residual (the next correction source) and its norm.
+mg_status mixed_tail(mg_hierarchy* h) {
   for (int l = h->base; l <= finest(h); ++l) {
     DevLevel& L = h->L[l];
     KL(MG_K_PROLONG, cells_of(L.G),
@@ -853,6 +1009,11 @@ mg_status mixed_outer_body(mg_hierarchy* h) {
   }
   for (int l = h->base + 1; l <= finest(h); ++l) ST(tangential<double>(h, l));
   return norm_launches(h);
+}
+
+mg_status mixed_outer_body(mg_hierarchy* h) {
+  ST(mixed_inner(h));
+  return mixed_tail(h);
 }
 
 // f on the leaf levels holds the source: remove its composite mean.
@@ -1169,7 +1330,8 @@ mg_status loop_read(mg_hierarchy* h, SolveState& st, const LoopState* rec = null
   if (h->mixed) h->inner_now = R.inner_now;
   if (R.timeout)
     return fail(h, MG_ETIMEOUT,
-                "a smoother block's wait for a staged plane tile ran out; outputs are invalid");
+                "a bounded device-side wait ran out (a smoother block's wait for a staged plane "
+                "tile, or a persistent batch item's wait for its dependency); outputs are invalid");
   return MG_OK;
 }
 
@@ -1402,6 +1564,10 @@ namespace {
 struct BatchGraph {
   cudaGraphExec_t exec = nullptr;
   std::vector<mg_stats> delta;  // launch counts each member adds per replay
+  // persistent mode: the work list, member weights and launch state (one allocation)
+  void* dbuf = nullptr;
+  long long items = 0;  // work items per replay
+  int ops = 0;          // level operations per replay
 };
 
 }  // namespace
@@ -1439,10 +1605,137 @@ mg_status member_status(mg_batch* b, int i, mg_status st) {
   return st;
 }
 
+// Every member is MG_MIXED with MG_FLAG_PERSISTENT (and no device-side loop): the
+// float32 halves of their outer iterations run as one persistent launch.
+bool batch_persistent(const mg_batch* b) {
+  for (const mg_hierarchy* h : b->m)
+    if (!h->mixed || !(h->cfg.flags & MG_FLAG_PERSISTENT) || (h->cfg.flags & MG_FLAG_NO_GRAPHS))
+      return false;
+  return true;
+}
+
+constexpr unsigned long long kPersistWaitNs = 2000000000ull;  // 2 s per dependency wait
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Persistent mode: the active members' float32 halves are recorded as work lists (the
+// members' host state advances as for a capture), merged in chain order, uploaded, and
+// captured as [reset state, persistent launch, wait flags] followed by each member's
+// float64 half on its own stream.
+mg_status batch_graph_persistent(mg_batch* b, const std::vector<int>& active, BatchGraph& g) {
+  const size_t n = b->m.size();
+  std::vector<std::vector<POp>> lists(n);
+  for (size_t i = 0; i < n; ++i) {
+    if (!active[i]) continue;
+    mg_hierarchy* h = b->m[i];
+    h->rec = &lists[i];
+    const mg_status st = mixed_inner(h);
+    h->rec = nullptr;
+    if (st != MG_OK) return member_status(b, (int)i, st);
+  }
+  std::vector<POp> ops;
+  long long total = 0;
+  size_t longest = 0;
+  for (size_t i = 0; i < n; ++i) longest = std::max(longest, lists[i].size());
+  for (size_t q = 0; q < longest; ++q)
+    for (size_t i = 0; i < n; ++i) {
+      if (!active[i] || q >= lists[i].size()) continue;
+      POp o = lists[i][q];
+      o.member = (int)i;
+      o.seq = (int)q;
+      o.tile0 = total;
+      total += o.ntiles;
+      ops.push_back(o);
+    }
+  if (ops.empty()) return bfail(b, MG_EINVAL, "persistent batch: empty work list");
+  const size_t wb = persist_weight_bytes();
+  const size_t off_w = align_up(ops.size() * sizeof(POp), 256);
+  const size_t off_f = align_up(off_w + n * wb, 256);                  // member wait flags
+  const size_t off_s = align_up(off_f + n * sizeof(unsigned*), 256);   // PState
+  const size_t off_d = off_s + align_up(sizeof(PState), 16);           // done[n]
+  const size_t off_c = off_d + align_up(n * sizeof(int), 16);          // count[ops]
+  const size_t bytes = off_c + ops.size() * sizeof(int);
+  std::vector<unsigned char> host(off_s, 0);
+  std::memcpy(host.data(), ops.data(), ops.size() * sizeof(POp));
+  std::vector<unsigned*> flags(n, nullptr);
+  for (size_t i = 0; i < n; ++i) {
+    persist_weights(b->m[i]->w, host.data() + off_w + i * wb);
+    flags[i] = active[i] ? b->m[i]->wait_err : nullptr;
+  }
+  std::memcpy(host.data() + off_f, flags.data(), n * sizeof(unsigned*));
+  int grid = 0;
+  BCK(persist_grid(&grid));
+  char* d = nullptr;
+  BCK(cudaMalloc(&d, bytes));
+  g.dbuf = d;
+  g.items = total;
+  g.ops = (int)ops.size();
+  BCK(cudaMemcpy(d, host.data(), off_s, cudaMemcpyHostToDevice));
+  PState* st = reinterpret_cast<PState*>(d + off_s);
+  int* done = reinterpret_cast<int*>(d + off_d);
+  int* count = reinterpret_cast<int*>(d + off_c);
+
+  BCK(cudaStreamBeginCapture(b->s, cudaStreamCaptureModeRelaxed));
+  mg_status rs = MG_OK;
+  cudaError_t e = cudaMemsetAsync(d + off_s, 0, bytes - off_s, b->s);
+  if (e == cudaSuccess)
+    e = launch_persist(reinterpret_cast<const POp*>(d), (int)ops.size(), total, d + off_w, st, done,
+                       count, kPersistWaitNs, grid, b->s);
+  if (e == cudaSuccess)
+    e = launch_persist_flags(st, reinterpret_cast<unsigned* const*>(d + off_f), (int)n, b->s);
+  if (e == cudaSuccess) e = cudaEventRecord(b->fork, b->s);
+  for (size_t i = 0; i < n && rs == MG_OK && e == cudaSuccess; ++i) {
+    if (!active[i]) continue;
+    mg_hierarchy* h = b->m[i];
+    e = cudaStreamWaitEvent(h->s, b->fork, 0);
+    if (e != cudaSuccess) break;
+    const mg_stats snap = h->stats;
+    const unsigned keep = h->active_mask;
+    h->active_mask = 0;
+    rs = mixed_tail(h);
+    h->active_mask = keep;
+    for (int f = 0; f < MG_K_FAMILIES; ++f) {
+      g.delta[i].launches[f] = h->stats.launches[f] - snap.launches[f];
+      g.delta[i].cells[f] = h->stats.cells[f] - snap.cells[f];
+    }
+    h->stats = snap;
+    if (rs != MG_OK) {
+      member_status(b, (int)i, rs);
+      break;
+    }
+    e = cudaEventRecord(b->join[i], h->s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->s, b->join[i], 0);
+  }
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(b->s, &graph);
+  if (rs != MG_OK || e != cudaSuccess || ee != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    if (rs != MG_OK) return rs;
+    BCK(e != cudaSuccess ? e : ee);
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  BCK(ei);
+  return MG_OK;
+}
+
 mg_status batch_graph(mg_batch* b, const std::vector<int>& active, BatchGraph** out) {
   auto it = b->graphs.find(active);
   if (it != b->graphs.end()) {
     *out = &it->second;
+    return MG_OK;
+  }
+  if (batch_persistent(b)) {
+    BatchGraph g;
+    g.delta.resize(b->m.size());
+    const mg_status st = batch_graph_persistent(b, active, g);
+    if (st != MG_OK) {
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      if (g.dbuf) cudaFree(g.dbuf);
+      return st;
+    }
+    auto res = b->graphs.emplace(active, g);
+    *out = &res.first->second;
     return MG_OK;
   }
   BatchGraph g;
@@ -1874,8 +2167,10 @@ mg_status mg_batch_create(mg_hierarchy* const members[], int count, void* cuda_s
 mg_status mg_batch_destroy(mg_batch* b) {
   if (!b) return MG_OK;
   if (b->s) cudaStreamSynchronize(b->s);
-  for (auto& kv : b->graphs)
+  for (auto& kv : b->graphs) {
     if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.dbuf) cudaFree(kv.second.dbuf);
+  }
   for (cudaEvent_t e : b->join)
     if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : b->ready)

@@ -31,6 +31,13 @@ __host__ __device__ inline long long gidx(const Grid& G, int i, int j, int k) {
 
 inline long long grid_elems(const Grid& G) { return (long long)G.X * G.Y * G.Zp; }
 
+// Ghost cells of a periodic level's shell (the periodic ghost fill's thread count).
+__host__ __device__ inline long long ghost_shell_count(const Grid& G) {
+  const long long g = G.g;
+  const long long X = G.n0 + 2 * g, Y = G.n1 + 2 * g;
+  return X * Y * 2 * g + X * 2 * g * G.n2 + 2 * g * (long long)G.n1 * G.n2;
+}
+
 Grid make_grid(int n0, int n1, int n2, int g);
 
 struct Int3 {

@@ -3,6 +3,7 @@
 // displacement gradient (Hahn & Abel 2011, Sec. 3.1, 3.2).
 #include "mg_internal.h"
 #include "mg_stencil.cuh"
+#include "mg_vbody.cuh"
 
 namespace mgk {
 
@@ -41,38 +42,13 @@ __device__ __forceinline__ double lap_w(int s) {
 // u(x) = sum_y K(x - y) f(y), K precomputed on the host from the DFT symbol.
 // One block per output cell; the block's threads split the sum over y.  The
 // result is also written to the cell's periodic ghost images.
-constexpr int kCoarseBlock = 128;
+constexpr int kCoarseBlock = kCoarseThreads;
 
 template <typename T>
 __global__ void __launch_bounds__(kCoarseBlock)
     k_coarsest(Grid G, const T* __restrict__ f, T* __restrict__ u,
                const double* __restrict__ kern) {
-  const int n12 = G.n1 * G.n2;
-  const int n = G.n0 * n12;
-  const int x = blockIdx.x;
-  const int xk = x % G.n2, xj = (x / G.n2) % G.n1, xi = x / n12;
-  double acc = 0.0;
-  for (int y = threadIdx.x; y < n; y += kCoarseBlock) {
-    const int yk = y % G.n2, yj = (y / G.n2) % G.n1, yi = y / n12;
-    int di = xi - yi, dj = xj - yj, dk = xk - yk;
-    di += di < 0 ? G.n0 : 0;
-    dj += dj < 0 ? G.n1 : 0;
-    dk += dk < 0 ? G.n2 : 0;
-    acc = fma(__ldg(kern + (di * G.n1 + dj) * G.n2 + dk), (double)__ldg(f + gidx(G, yi, yj, yk)), acc);
-  }
-  __shared__ double red[kCoarseBlock];
-  red[threadIdx.x] = acc;
-  __syncthreads();
-#pragma unroll
-  for (int w = kCoarseBlock / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    const T v = (T)red[0];
-    u[gidx(G, xi, xj, xk)] = v;
-    write_images<T>(G, u, xi, xj, xk, v);
-  }
+  coarsest_body<T, Ldg>(G, f, u, kern, (int)blockIdx.x, (int)threadIdx.x);
 }
 
 template <int BLOCK>

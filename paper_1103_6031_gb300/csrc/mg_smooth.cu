@@ -10,12 +10,13 @@
 // thread ever reads a value another thread of the same launch writes.
 #include "mg_internal.h"
 #include "mg_stencil.cuh"
+#include "mg_vbody.cuh"
 
 namespace mgk {
 
 namespace {
 
-constexpr int kPairX = 32;  // z-pairs per block row; blockDim.y = rows (1..8)
+constexpr int kPairX = kVPairX;  // z-pairs per block row; blockDim.y = rows (1..8)
 // At least 5 blocks of up to 256 threads per SM: caps the smoother at 48 registers
 // (80 unbounded).  Measured on GB300 in CUDA graphs: float32 half-sweeps 15-20%
 // faster at 128^3 (more warps in flight for the L1-bound loads), float64 unchanged
@@ -28,47 +29,9 @@ template <int ORDER, typename T>
 __global__ void __launch_bounds__(kPairX * 8, MG_SMOOTH_MIN_BLOCKS)
     k_smooth_half(Grid G, const T* __restrict__ uin, T* __restrict__ uout,
                   const T* __restrict__ f, T a_f, int colour, int periodic) {
-  const int t = blockIdx.x * kPairX + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int i = blockIdx.z;
-  const int k0 = 2 * t;
-  if (j >= G.n1 || k0 >= G.n2) return;
-  const long long sy = G.Zp;
-  const long long sx = (long long)G.Y * G.Zp;
-  const long long p0 = gidx(G, i, j, k0);
-  const int upd = (((i + j + k0) & 1) == colour) ? 0 : 1;
-  const bool pair = (k0 + 1) < G.n2;
-  if (!pair && upd == 1) {
-    const T c = __ldg(uin + p0);
-    uout[p0] = c;
-    if (periodic) write_images<T>(G, uout, i, j, k0, c);
-    return;
-  }
-  const long long p = p0 + upd;
-  T s1, s2, s3;
-  neighbour_sums<ORDER, T>(uin, p, sy, sx, s1, s2, s3);
-  // u = (h^2 f - sum_off w u_nb) / w_centre
-  constexpr double wc = 3.0 * Lap<ORDER>::w0;
-  T v = a_f * __ldg(f + p);
-  v = fma(T(-Lap<ORDER>::w1 / wc), s1, v);
-  if (ORDER >= 4) v = fma(T(-Lap<ORDER>::w2 / wc), s2, v);
-  if (ORDER >= 6) v = fma(T(-Lap<ORDER>::w3 / wc), s3, v);
-  if (pair) {
-    typedef typename Vec2<T>::type V2;
-    V2 out;
-    if (upd == 0) {
-      out.x = v;
-      out.y = __ldg(uin + p0 + 1);
-    } else {
-      out.x = __ldg(uin + p0);
-      out.y = v;
-    }
-    *reinterpret_cast<V2*>(uout + p0) = out;
-    if (periodic) write_pair_images<T>(G, uout, i, j, k0, out.x, out.y);
-  } else {
-    uout[p0] = v;
-    if (periodic) write_images<T>(G, uout, i, j, k0, v);
-  }
+  smooth_half_body<ORDER, T, Ldg>(G, uin, uout, f, a_f, colour, periodic, (int)blockDim.y,
+                                  Blk{(int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z,
+                                      (int)threadIdx.x, (int)threadIdx.y});
 }
 
 // One thread per covered parent cell: r = f - L u at its 8 children,
@@ -78,32 +41,10 @@ __global__ void __launch_bounds__(128)
     k_residual_restrict(Grid F, const T* __restrict__ u, const T* __restrict__ f, T invh2, Grid P,
                         T* __restrict__ pu, T* __restrict__ pfas, T* __restrict__ ubar, Int3 off,
                         Int3 cn, int parent_periodic) {
-  const int kc = blockIdx.x * blockDim.x + threadIdx.x;
-  const int jc = blockIdx.y * blockDim.y + threadIdx.y;
-  const int ic = blockIdx.z;
-  if (kc >= cn.z || jc >= cn.y) return;
-  const long long sy = F.Zp;
-  const long long sx = (long long)F.Y * F.Zp;
-  T su = T(0), sr = T(0);
-#pragma unroll
-  for (int di = 0; di < 2; ++di) {
-#pragma unroll
-    for (int dj = 0; dj < 2; ++dj) {
-#pragma unroll
-      for (int dk = 0; dk < 2; ++dk) {
-        const long long p = gidx(F, 2 * ic + di, 2 * jc + dj, 2 * kc + dk);
-        const T lu = lap_h2<ORDER, T>(u, p, sy, sx);
-        su += __ldg(u + p);
-        sr += fma(-invh2, lu, __ldg(f + p));
-      }
-    }
-  }
-  const long long q = gidx(P, off.x + ic, off.y + jc, off.z + kc);
-  const T mu = su * T(0.125);
-  pu[q] = mu;
-  if (parent_periodic) write_images<T>(P, pu, off.x + ic, off.y + jc, off.z + kc, mu);
-  pfas[q] = sr * T(0.125);
-  ubar[((long long)ic * cn.y + jc) * cn.z + kc] = mu;
+  residual_restrict_body<ORDER, T, Ldg>(F, u, f, invh2, P, pu, pfas, ubar, off, cn,
+                                        parent_periodic,
+                                        Blk{(int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z,
+                                            (int)threadIdx.x, (int)threadIdx.y});
 }
 
 // Covered parent cells: f_fas += L u (u = restricted fine solution there).
@@ -111,14 +52,9 @@ template <int ORDER, typename T>
 __global__ void __launch_bounds__(128)
     k_fas_source(Grid P, const T* __restrict__ pu, T* __restrict__ pfas, T invH2, Int3 off,
                  Int3 cn) {
-  const int kc = blockIdx.x * blockDim.x + threadIdx.x;
-  const int jc = blockIdx.y * blockDim.y + threadIdx.y;
-  const int ic = blockIdx.z;
-  if (kc >= cn.z || jc >= cn.y) return;
-  const long long sy = P.Zp;
-  const long long sx = (long long)P.Y * P.Zp;
-  const long long q = gidx(P, off.x + ic, off.y + jc, off.z + kc);
-  pfas[q] = fma(invH2, lap_h2<ORDER, T>(pu, q, sy, sx), pfas[q]);
+  fas_source_body<ORDER, T, Ldg>(P, pu, pfas, invH2, off, cn,
+                                 Blk{(int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z,
+                                     (int)threadIdx.x, (int)threadIdx.y});
 }
 
 // u += inject(parent u - ubar) on the fine interior; one thread per z-pair.
@@ -126,24 +62,9 @@ template <typename T>
 __global__ void __launch_bounds__(128)
     k_prolong(Grid F, T* __restrict__ u, Grid P, const T* __restrict__ pu,
               const T* __restrict__ ubar, Int3 off, Int3 cn, int periodic) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int i = blockIdx.z;
-  const int k0 = 2 * t;
-  if (j >= F.n1 || k0 >= F.n2) return;
-  const int ic = i >> 1, jc = j >> 1, kc = t;
-  const T d = __ldg(pu + gidx(P, off.x + ic, off.y + jc, off.z + kc)) -
-              __ldg(ubar + ((long long)ic * cn.y + jc) * cn.z + kc);
-  const long long p = gidx(F, i, j, k0);
-  typedef typename Vec2<T>::type V2;
-  V2 v = *reinterpret_cast<const V2*>(u + p);
-  v.x += d;
-  v.y += d;
-  *reinterpret_cast<V2*>(u + p) = v;
-  if (periodic) {
-    if (k0 + 1 < F.n2) write_pair_images<T>(F, u, i, j, k0, v.x, v.y);
-    else write_images<T>(F, u, i, j, k0, v.x);
-  }
+  prolong_body<T, Ldg>(F, u, P, pu, ubar, off, cn, periodic,
+                       Blk{(int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)threadIdx.x,
+                           (int)threadIdx.y});
 }
 
 // parent u := mean of children (covered region), one thread per parent cell.

@@ -24,31 +24,44 @@ struct Lap<6> {
                           w3 = 2.0 / 180.0;
 };
 
+// Load policies.  Ldg: the read-only data path, for kernels whose inputs no thread of
+// the launch writes.  Weak: plain loads, for the persistent kernel, whose work items
+// read what earlier items of the same launch wrote (ordered by release/acquire
+// flags, which the read-only path does not observe).
+struct Ldg {
+  template <typename T>
+  static __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
+};
+struct Weak {
+  template <typename T>
+  static __device__ __forceinline__ T ld(const T* p) { return *p; }
+};
+
 // Sums of the 6 neighbours at distance d = 1, 2, 3 (axis-aligned) of element p.
-template <int ORDER, typename T>
+template <int ORDER, typename T, typename LD = Ldg>
 __device__ __forceinline__ void neighbour_sums(const T* __restrict__ u, long long p, long long sy,
                                                long long sx, T& s1, T& s2, T& s3) {
-  s1 = (__ldg(u + p - 1) + __ldg(u + p + 1)) + (__ldg(u + p - sy) + __ldg(u + p + sy)) +
-       (__ldg(u + p - sx) + __ldg(u + p + sx));
+  s1 = (LD::ld(u + p - 1) + LD::ld(u + p + 1)) + (LD::ld(u + p - sy) + LD::ld(u + p + sy)) +
+       (LD::ld(u + p - sx) + LD::ld(u + p + sx));
   s2 = T(0);
   s3 = T(0);
   if (ORDER >= 4) {
-    s2 = (__ldg(u + p - 2) + __ldg(u + p + 2)) + (__ldg(u + p - 2 * sy) + __ldg(u + p + 2 * sy)) +
-         (__ldg(u + p - 2 * sx) + __ldg(u + p + 2 * sx));
+    s2 = (LD::ld(u + p - 2) + LD::ld(u + p + 2)) + (LD::ld(u + p - 2 * sy) + LD::ld(u + p + 2 * sy)) +
+         (LD::ld(u + p - 2 * sx) + LD::ld(u + p + 2 * sx));
   }
   if (ORDER >= 6) {
-    s3 = (__ldg(u + p - 3) + __ldg(u + p + 3)) + (__ldg(u + p - 3 * sy) + __ldg(u + p + 3 * sy)) +
-         (__ldg(u + p - 3 * sx) + __ldg(u + p + 3 * sx));
+    s3 = (LD::ld(u + p - 3) + LD::ld(u + p + 3)) + (LD::ld(u + p - 3 * sy) + LD::ld(u + p + 3 * sy)) +
+         (LD::ld(u + p - 3 * sx) + LD::ld(u + p + 3 * sx));
   }
 }
 
 // h^2 L u at element p.
-template <int ORDER, typename T>
+template <int ORDER, typename T, typename LD = Ldg>
 __device__ __forceinline__ T lap_h2(const T* __restrict__ u, long long p, long long sy,
                                     long long sx) {
   T s1, s2, s3;
-  neighbour_sums<ORDER, T>(u, p, sy, sx, s1, s2, s3);
-  T acc = T(3.0 * Lap<ORDER>::w0) * __ldg(u + p);
+  neighbour_sums<ORDER, T, LD>(u, p, sy, sx, s1, s2, s3);
+  T acc = T(3.0 * Lap<ORDER>::w0) * LD::ld(u + p);
   acc = fma(T(Lap<ORDER>::w1), s1, acc);
   if (ORDER >= 4) acc = fma(T(Lap<ORDER>::w2), s2, acc);
   if (ORDER >= 6) acc = fma(T(Lap<ORDER>::w3), s3, acc);

@@ -18,6 +18,7 @@ MG_FLAG_NO_TMA = 2
 MG_FLAG_TMA_ALL = 4
 MG_FLAG_HYBRID = 8
 MG_FLAG_DEVICE_LOOP = 16
+MG_FLAG_PERSISTENT = 32
 _TMA_FLAGS = {"auto": 0, "off": MG_FLAG_NO_TMA, "all": MG_FLAG_TMA_ALL}
 
 STATUS = {0: "MG_OK", 1: "MG_EINVAL", 2: "MG_ENOMEM", 3: "MG_ENOCONV", 4: "MG_ECUDA",
@@ -166,6 +167,7 @@ def load_library(path=None):
         "mg_last_error": (ctypes.c_char_p, [vp]),
         "mg_selftest_wait_limit": (ctypes.c_int, []),
         "mg_fp64_fma_rate": (ctypes.c_int, [ctypes.c_int, vp, ctypes.POINTER(ctypes.c_double)]),
+        "mg_selftest_persist_wait": (ctypes.c_int, []),
         "mg_hybrid_correction": (ctypes.c_int, [vp, vp, ctypes.POINTER(vp)]),
         "mg_lla_density": (ctypes.c_int, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_double,
                                           ctypes.c_double, ctypes.POINTER(vp)]),
@@ -200,14 +202,17 @@ def load_library(path=None):
 
 def make_config(base_n, box, order, nests=(), precision=MG_FP64, nu1=2, nu2=2, max_cycles=50,
                 tol=1e-10, inner_cycles=2, graphs=True, tile_rows=4, tma="auto", hybrid=False,
-                device_loop=False):
+                device_loop=False, persistent=False):
     """MGConfig from plain values; nests = [(n3, off3), ...] (off in parent cells).
     tma: smoother kernel choice, "auto" (TMA-staged tiles on float32 nests of
     >= 2^23 cells), "off" or "all"; every choice gives bit-identical results.
     hybrid: the pipelines add the hybrid Poisson correction (Sec. 3.5.2) to the
     finest level's displacements.
     device_loop: the iteration loop of every solve runs on the device (one CUDA
-    graph with a while node per solve; same launches and results)."""
+    graph with a while node per solve; same launches and results).
+    persistent: in a Batch of mixed-precision members that all set it, the float32
+    V-cycles of all members run as one persistent kernel launch per outer iteration
+    (same results)."""
     lib = load_library()
     cfg = MGConfig()
     lib.mg_config_default(ctypes.byref(cfg))
@@ -224,7 +229,8 @@ def make_config(base_n, box, order, nests=(), precision=MG_FP64, nu1=2, nu2=2, m
     cfg.nu1, cfg.nu2, cfg.max_cycles, cfg.tol = int(nu1), int(nu2), int(max_cycles), float(tol)
     cfg.inner_cycles = int(inner_cycles)
     cfg.flags = (0 if graphs else MG_FLAG_NO_GRAPHS) | _TMA_FLAGS[tma] | \
-        (MG_FLAG_HYBRID if hybrid else 0) | (MG_FLAG_DEVICE_LOOP if device_loop else 0)
+        (MG_FLAG_HYBRID if hybrid else 0) | (MG_FLAG_DEVICE_LOOP if device_loop else 0) | \
+        (MG_FLAG_PERSISTENT if persistent else 0)
     cfg.tile_rows = int(tile_rows)
     return cfg
 
@@ -478,6 +484,12 @@ def selftest_wait_limit():
     """Runs the device wait-limit self-test (about 2 s); returns the status name,
     "MG_ETIMEOUT" when the bounded wait and its error path work."""
     return STATUS.get(int(load_library().mg_selftest_wait_limit()), "unknown")
+
+
+def selftest_persist_wait():
+    """Runs the persistent batch kernel's wait-limit self-test (about 0.1 s); returns
+    the status name, "MG_ETIMEOUT" when the bounded wait and its error path work."""
+    return STATUS.get(int(load_library().mg_selftest_persist_wait()), "unknown")
 
 
 def fp64_fma_rate(iters=4096, stream=None):

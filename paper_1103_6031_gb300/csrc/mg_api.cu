@@ -1619,9 +1619,9 @@ constexpr unsigned long long kPersistWaitNs = 2000000000ull;  // 2 s per depende
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // Persistent mode: the active members' float32 halves are recorded as work lists (the
-// members' host state advances as for a capture), merged in chain order, uploaded, and
-// captured as [reset state, persistent launch, wait flags] followed by each member's
-// float64 half on its own stream.
+// members' host state advances as for a capture), uploaded, and captured as [reset
+// state, persistent launch, wait flags] followed by each member's float64 half on its
+// own stream.
 mg_status batch_graph_persistent(mg_batch* b, const std::vector<int>& active, BatchGraph& g) {
   const size_t n = b->m.size();
   std::vector<std::vector<POp>> lists(n);
@@ -1633,27 +1633,38 @@ mg_status batch_graph_persistent(mg_batch* b, const std::vector<int>& active, Ba
     h->rec = nullptr;
     if (st != MG_OK) return member_status(b, (int)i, st);
   }
+  // member-major work list: member i's chain at ops[mop0[i] .. mop0[i] + mops[i]), its
+  // items numbered along the chain
   std::vector<POp> ops;
+  std::vector<int> mop0(n, 0), mops(n, 0);
   long long total = 0;
-  size_t longest = 0;
-  for (size_t i = 0; i < n; ++i) longest = std::max(longest, lists[i].size());
-  for (size_t q = 0; q < longest; ++q)
-    for (size_t i = 0; i < n; ++i) {
-      if (!active[i] || q >= lists[i].size()) continue;
+  int active_n = 0;
+  for (size_t i = 0; i < n; ++i) {
+    mop0[i] = (int)ops.size();
+    if (!active[i]) continue;
+    ++active_n;
+    long long t = 0;
+    for (size_t q = 0; q < lists[i].size(); ++q) {
       POp o = lists[i][q];
       o.member = (int)i;
       o.seq = (int)q;
-      o.tile0 = total;
-      total += o.ntiles;
+      o.tile0 = t;
+      t += o.ntiles;
       ops.push_back(o);
     }
-  if (ops.empty()) return bfail(b, MG_EINVAL, "persistent batch: empty work list");
+    if (t > (1ll << 30)) return bfail(b, MG_EINVAL, "persistent batch: work list too long");
+    mops[i] = (int)lists[i].size();
+    total += t;
+  }
+  if (ops.empty() || active_n == 0) return bfail(b, MG_EINVAL, "persistent batch: empty work list");
   const size_t wb = persist_weight_bytes();
   const size_t off_w = align_up(ops.size() * sizeof(POp), 256);
   const size_t off_f = align_up(off_w + n * wb, 256);                  // member wait flags
-  const size_t off_s = align_up(off_f + n * sizeof(unsigned*), 256);   // PState
+  const size_t off_m = align_up(off_f + n * sizeof(unsigned*), 256);   // mop0[n], mops[n]
+  const size_t off_s = align_up(off_m + 2 * n * sizeof(int), 256);     // PState
   const size_t off_d = off_s + align_up(sizeof(PState), 16);           // done[n]
-  const size_t off_c = off_d + align_up(n * sizeof(int), 16);          // count[ops]
+  const size_t off_t = off_d + align_up(n * sizeof(int), 16);          // taken[n]
+  const size_t off_c = off_t + align_up(n * sizeof(int), 16);          // count[ops]
   const size_t bytes = off_c + ops.size() * sizeof(int);
   std::vector<unsigned char> host(off_s, 0);
   std::memcpy(host.data(), ops.data(), ops.size() * sizeof(POp));
@@ -1663,6 +1674,8 @@ mg_status batch_graph_persistent(mg_batch* b, const std::vector<int>& active, Ba
     flags[i] = active[i] ? b->m[i]->wait_err : nullptr;
   }
   std::memcpy(host.data() + off_f, flags.data(), n * sizeof(unsigned*));
+  std::memcpy(host.data() + off_m, mop0.data(), n * sizeof(int));
+  std::memcpy(host.data() + off_m + n * sizeof(int), mops.data(), n * sizeof(int));
   int grid = 0;
   BCK(persist_grid(&grid));
   char* d = nullptr;
@@ -1673,14 +1686,16 @@ mg_status batch_graph_persistent(mg_batch* b, const std::vector<int>& active, Ba
   BCK(cudaMemcpy(d, host.data(), off_s, cudaMemcpyHostToDevice));
   PState* st = reinterpret_cast<PState*>(d + off_s);
   int* done = reinterpret_cast<int*>(d + off_d);
+  int* taken = reinterpret_cast<int*>(d + off_t);
   int* count = reinterpret_cast<int*>(d + off_c);
+  const int* dmop0 = reinterpret_cast<const int*>(d + off_m);
 
   BCK(cudaStreamBeginCapture(b->s, cudaStreamCaptureModeRelaxed));
   mg_status rs = MG_OK;
   cudaError_t e = cudaMemsetAsync(d + off_s, 0, bytes - off_s, b->s);
   if (e == cudaSuccess)
-    e = launch_persist(reinterpret_cast<const POp*>(d), (int)ops.size(), total, d + off_w, st, done,
-                       count, kPersistWaitNs, grid, b->s);
+    e = launch_persist(reinterpret_cast<const POp*>(d), dmop0, dmop0 + n, (int)n, active_n,
+                       d + off_w, st, done, taken, count, kPersistWaitNs, grid, b->s);
   if (e == cudaSuccess)
     e = launch_persist_flags(st, reinterpret_cast<unsigned* const*>(d + off_f), (int)n, b->s);
   if (e == cudaSuccess) e = cudaEventRecord(b->fork, b->s);

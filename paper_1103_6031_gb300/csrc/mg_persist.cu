@@ -1,17 +1,18 @@
 // The persistent batch kernel: the float32 V-cycles of many hierarchies in one launch
 // over a work list of (hierarchy, level operation, block range) items.
 //
-// A block of 128 threads repeatedly takes the next item (one atomic counter), waits
-// until its hierarchy has completed every earlier operation of its chain (a per-
-// hierarchy counter read with acquire semantics; the wait is bounded by wait_ns of
-// global time and polls the launch's error word), runs the item's blocks through the
-// same bodies the stream kernels run (mg_vbody.cuh, with plain loads, since items read
-// what earlier items of the launch wrote), and counts the item done; the block that
-// completes an operation's last item publishes the hierarchy's counter with release
-// semantics.  Items are handed out in chain order, so every item a block waits for
-// was handed out earlier to a block that is running: with every block resident, the
-// launch cannot deadlock; a wait that still runs out (a defect) sets the error word,
-// and every block stops at its next wait or item.
+// Each hierarchy's operations form a chain (ops[mop0[m] .. mop0[m] + mops[m]), items
+// numbered along the chain); only the first incomplete operation of a chain is open.
+// A block of 128 threads scans the hierarchies (from a rotating start) for one whose
+// open operation still has items, takes one with a compare-and-swap on that chain's
+// item counter, runs the item's blocks through the same bodies the stream kernels run
+// (mg_vbody.cuh, with plain loads, since items read what earlier items of the launch
+// wrote), and counts it done; the block that completes an operation's last item opens
+// the next one by publishing the chain's done counter with release semantics (takers
+// read it with acquire semantics).  A block never waits on an item it holds, so every
+// taken item completes; a block that finds nothing open waits, and a wait longer than
+// wait_ns without a single item (a defect: no chain can advance) sets the error word,
+// after which every block stops.
 #include <cstring>
 #include <vector>
 
@@ -96,53 +97,70 @@ __device__ __forceinline__ void run_block(const POp& op, const CfW<float>& w, in
 }
 
 __global__ void __launch_bounds__(kPersistThreads)
-    k_persist(const POp* __restrict__ ops, int nops, long long total,
-              const CfW<float>* __restrict__ wts, PState* st, int* done, int* count,
-              unsigned long long wait_ns) {
-  __shared__ int s_op;
-  __shared__ long long s_item;
-  __shared__ int s_go;
+    k_persist(const POp* __restrict__ ops, const int* __restrict__ mop0, const int* __restrict__ mops,
+              int members, int active, const CfW<float>* __restrict__ wts, PState* st, int* done,
+              int* taken, int* count, unsigned long long wait_ns) {
+  __shared__ int s_op, s_lt, s_go;
+  unsigned long long idle_since = 0;
+  int start = (int)(blockIdx.x % (unsigned)members);
   for (;;) {
     if (threadIdx.x == 0) {
-      int go = 0, j = 0;
-      const long long it = (long long)atomicAdd(&st->next, 1ULL);
-      if (it < total && ld_volatile(&st->err) == 0u) {
-        // the op whose items hold `it`: the last j with ops[j].tile0 <= it
-        int lo = 0, hi = nops - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (ops[mid].tile0 <= it) lo = mid;
-          else hi = mid - 1;
-        }
-        j = lo;
-        const int m = ops[j].member, seq = ops[j].seq;
-        go = 1;
-        if (ld_acquire(done + m) < seq) {
-          const unsigned long long t0 = global_ns();
-          while (ld_acquire(done + m) < seq) {
-            if (ld_volatile(&st->err) != 0u) {
-              go = 0;
+      int go = 0, jo = 0, lt = 0;
+      if (ld_volatile(&st->err) != 0u) {
+        go = -1;
+      } else {
+        // the first member (scanning from this block's rotating start) whose open
+        // operation still has items: take one with a compare-and-swap
+        for (int k = 0; k < members && go == 0; ++k) {
+          const int m = (start + k) % members;
+          const int d = ld_acquire(done + m);
+          if (d >= mops[m]) continue;
+          const int j = mop0[m] + d;
+          const int end = (int)ops[j].tile0 + ops[j].ntiles;
+          int t = *reinterpret_cast<volatile int*>(taken + m);
+          while (t < end) {
+            const int old = atomicCAS(taken + m, t, t + 1);
+            if (old == t) {
+              go = 1;
+              jo = j;
+              lt = t - (int)ops[j].tile0;
               break;
             }
-            if (global_ns() - t0 > wait_ns) {
-              atomicOr(&st->err, 1u);
-              go = 0;
-              break;
-            }
-            __nanosleep(128);
+            t = old;
           }
         }
+        start = (start + 1) % members;
+        if (go == 0) {
+          if (ld_volatile(&st->finished) >= (unsigned)active) {
+            go = -1;  // every member's chain is complete
+          } else {
+            const unsigned long long now = global_ns();
+            if (idle_since == 0) idle_since = now;
+            if (now - idle_since > wait_ns) {
+              atomicOr(&st->err, 1u);
+              go = -1;
+            } else {
+              __nanosleep(256);
+            }
+          }
+        } else {
+          idle_since = 0;
+        }
       }
-      s_item = it;
-      s_op = j;
       s_go = go;
+      s_op = jo;
+      s_lt = lt;
     }
     __syncthreads();
-    if (!s_go) break;
+    const int go = s_go;
+    if (go < 0) break;
+    if (go == 0) {
+      __syncthreads();  // thread 0 rewrites s_* only after every thread has read them
+      continue;
+    }
     const POp& op = ops[s_op];
     const CfW<float>& w = wts[op.member];
-    const int lt = (int)(s_item - op.tile0);
-    const int b0 = lt * op.per_tile;
+    const int b0 = s_lt * op.per_tile;
     const int b1 = min(b0 + op.per_tile, op.nblk);
     for (int blk = b0; blk < b1; ++blk) {
       switch (op.order) {
@@ -155,7 +173,10 @@ __global__ void __launch_bounds__(kPersistThreads)
     __syncthreads();
     if (threadIdx.x == 0) {
       const int c = atomicAdd(count + s_op, 1) + 1;
-      if (c == op.ntiles) st_release(done + op.member, op.seq + 1);
+      if (c == op.ntiles) {
+        if (op.seq + 1 == mops[op.member]) atomicAdd(&st->finished, 1u);
+        st_release(done + op.member, op.seq + 1);
+      }
     }
   }
 }
@@ -174,13 +195,13 @@ cudaError_t launch_persist_flags(const PState* st, unsigned* const* flags, int n
   return cudaGetLastError();
 }
 
-cudaError_t launch_persist(const POp* ops, int nops, long long total, const void* wts,
-                           PState* st, int* done, int* count, unsigned long long wait_ns,
-                           int grid, cudaStream_t s) {
-  if (nops < 1 || total < 1 || grid < 1) return cudaErrorInvalidValue;
-  k_persist<<<grid, kPersistThreads, 0, s>>>(ops, nops, total,
+cudaError_t launch_persist(const POp* ops, const int* mop0, const int* mops, int members,
+                           int active, const void* wts, PState* st, int* done, int* taken,
+                           int* count, unsigned long long wait_ns, int grid, cudaStream_t s) {
+  if (members < 1 || active < 1 || grid < 1) return cudaErrorInvalidValue;
+  k_persist<<<grid, kPersistThreads, 0, s>>>(ops, mop0, mops, members, active,
                                              static_cast<const CfW<float>*>(wts), st, done,
-                                             count, wait_ns);
+                                             taken, count, wait_ns);
   return cudaGetLastError();
 }
 
@@ -204,18 +225,18 @@ void persist_weights(const CfWeights& w, void* dst) {
 
 }  // namespace mgk
 
-// Self-test of the bounded dependency wait (no counterpart in the paper): a work list
-// whose second item depends on an operation that does not exist, so its wait can never
-// be satisfied; with a 100 ms limit the block gives up, sets the error word and the
-// launch ends.
+// Self-test of the bounded wait (no counterpart in the paper): a launch whose blocks
+// are told to wait for a second hierarchy that has no work, so nothing ever opens;
+// with a 100 ms limit the blocks give up, set the error word and the launch ends.
 extern "C" mg_status mg_selftest_persist_wait(void) {
   using namespace mgk;
   auto up = [](size_t v) { return (v + 255) / 256 * 256; };  // every region 256-aligned
   const size_t off_w = up(2 * sizeof(POp));
   const size_t off_z = up(off_w + persist_weight_bytes());
   const size_t off_s = up(off_z + 1024 * sizeof(float));
-  const size_t off_d = up(off_s + sizeof(PState));
-  const size_t bytes = off_d + 4 * sizeof(int);
+  const size_t off_d = up(off_s + sizeof(PState));  // done[2], taken[2], count[2]
+  const size_t off_c = up(off_d + 6 * sizeof(int));  // mop0[2], mops[2]
+  const size_t bytes = off_c + 4 * sizeof(int);
   char* d = nullptr;
   if (cudaMalloc(&d, bytes) != cudaSuccess) return MG_ENOMEM;
   POp ops[2];
@@ -224,7 +245,7 @@ extern "C" mg_status mg_selftest_persist_wait(void) {
     ops[q].kind = P_ZERO;
     ops[q].order = 2;
     ops[q].member = 0;
-    ops[q].seq = q == 0 ? 0 : 2;  // seq 1 does not exist: the second wait never ends
+    ops[q].seq = q;
     ops[q].nblk = 1;
     ops[q].per_tile = 1;
     ops[q].ntiles = 1;
@@ -232,18 +253,25 @@ extern "C" mg_status mg_selftest_persist_wait(void) {
     ops[q].out0 = reinterpret_cast<float*>(d + off_z);
     ops[q].n = 1024;
   }
+  // member 0 owns both operations; the launch is told that 2 members are active, so
+  // after member 0's chain the blocks find nothing open and wait for a member that
+  // never finishes: the wait must give up
+  const int chain[4] = {0, 2, 2, 0};  // mop0[0..1], mops[0..1]
   std::vector<unsigned char> w(persist_weight_bytes(), 0);
   PState* st = reinterpret_cast<PState*>(d + off_s);
-  int* done = reinterpret_cast<int*>(d + off_d);  // done[1] (one member), then count[2]
-  int* count = done + 2;
+  int* done = reinterpret_cast<int*>(d + off_d);
+  int* taken = done + 2;
+  int* count = done + 4;
+  const int* mop0 = reinterpret_cast<const int*>(d + off_c);
   cudaStream_t s = nullptr;
   mg_status r = MG_OK;
   if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
       cudaMemcpyAsync(d, ops, sizeof(ops), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(d + off_w, w.data(), w.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemsetAsync(d + off_s, 0, bytes - off_s, s) != cudaSuccess ||
-      launch_persist(reinterpret_cast<const POp*>(d), 2, 2, d + off_w, st, done, count,
-                     100000000ull, 2, s) != cudaSuccess ||
+      cudaMemsetAsync(d + off_s, 0, off_c - off_s, s) != cudaSuccess ||
+      cudaMemcpyAsync(d + off_c, chain, sizeof(chain), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      launch_persist(reinterpret_cast<const POp*>(d), mop0, mop0 + 2, 2, 2, d + off_w, st, done,
+                     taken, count, 100000000ull, 2, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess) {
     r = MG_ECUDA;
   } else {

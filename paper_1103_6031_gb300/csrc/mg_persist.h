@@ -3,8 +3,8 @@
 // own V-cycles would make: smoother half-sweeps, coarse-fine ghosts, residual and
 // restriction, FAS source, coarsest solve, tangential interpolation, prolongation,
 // zero fills) form a chain; an operation's blocks are cut into work items, and items
-// run in the order (position in the chain, hierarchy), so every hierarchy advances at
-// once while each one's chain keeps its order.
+// of any hierarchy run as soon as that hierarchy's earlier operations have completed,
+// so every hierarchy advances at once while each one's chain keeps its order.
 #pragma once
 
 #include "mg_internal.h"
@@ -53,18 +53,21 @@ struct POp {
 
 // Device state of one launch: reset to zero before every launch.
 struct PState {
-  unsigned long long next;  // next work item to hand out
-  unsigned err;             // 1: a bounded wait ran out (or the self-test's limit)
-  unsigned pad;
+  unsigned finished;  // chains (hierarchies) whose every operation has completed
+  unsigned err;       // 1: a bounded wait ran out (or the self-test's limit)
 };
 
-// The persistent launch over ops[0, nops) (sorted by tile0, the items of op j being
-// [tile0, tile0 + ntiles)), total work items, member weights wts[member] (float), the
-// state st with done[members] and count[nops] after it.  wait_ns bounds every wait
-// for a dependency; a wait that runs out sets st->err and every block stops.
-cudaError_t launch_persist(const POp* ops, int nops, long long total, const void* wts,
-                           PState* st, int* done, int* count, unsigned long long wait_ns,
-                           int grid, cudaStream_t s);
+// The persistent launch.  ops: every member's chain, member-major (member m's
+// operations are ops[mop0[m] .. mop0[m] + mops[m]), in chain order, with seq = position
+// in the chain and tile0 = the chain-local number of the operation's first item);
+// members: entries of mop0/mops (a member not in this launch has mops = 0); active:
+// members with work; wts[member]: float weights; per member done[] (completed
+// operations) and taken[] (items taken), per operation count[] (items completed), all
+// zero at launch.  wait_ns bounds the time a block may find nothing to take; running
+// out sets st->err and every block stops.
+cudaError_t launch_persist(const POp* ops, const int* mop0, const int* mops, int members,
+                           int active, const void* wts, PState* st, int* done, int* taken,
+                           int* count, unsigned long long wait_ns, int grid, cudaStream_t s);
 // After a persistent launch: or 1 into *flags[i] (each non-null) when st->err is set,
 // so that every member's convergence read reports the timeout.
 cudaError_t launch_persist_flags(const PState* st, unsigned* const* flags, int n, cudaStream_t s);

@@ -8,8 +8,8 @@
 // item counter, runs the item's blocks through the same bodies the stream kernels run
 // (mg_vbody.cuh, with plain loads, since items read what earlier items of the launch
 // wrote), and counts it done; the block that completes an operation's last item opens
-// the next one by publishing the chain's done counter with release semantics (takers
-// read it with acquire semantics).  A block never waits on an item it holds, so every
+// the next one by publishing the chain's done counter with release semantics (a taker
+// orders its item after that release with an acquire fence).  A block never waits on an item it holds, so every
 // taken item completes; a block that finds nothing open waits, and a wait longer than
 // wait_ns without a single item (a defect: no chain can advance) sets the error word,
 // after which every block stops.
@@ -23,14 +23,12 @@ namespace mgk {
 
 namespace {
 
-__device__ __forceinline__ int ld_acquire(const int* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
 __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void fence_acquire() {
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
 }
 
 __device__ __forceinline__ unsigned ld_volatile(const unsigned* p) {
@@ -102,6 +100,7 @@ __global__ void __launch_bounds__(kPersistThreads)
               int* taken, int* count, unsigned long long wait_ns) {
   __shared__ int s_op, s_lt, s_go;
   unsigned long long idle_since = 0;
+  unsigned backoff = 32;
   int start = (int)(blockIdx.x % (unsigned)members);
   for (;;) {
     if (threadIdx.x == 0) {
@@ -110,10 +109,13 @@ __global__ void __launch_bounds__(kPersistThreads)
         go = -1;
       } else {
         // the first member (scanning from this block's rotating start) whose open
-        // operation still has items: take one with a compare-and-swap
+        // operation still has items: take one with a compare-and-swap.  The scan reads
+        // the chain counters with plain volatile loads (an acquire load would invalidate
+        // the SM's L1 for every member looked at); the item taken is then ordered after
+        // the release that opened it by one acquire fence.
         for (int k = 0; k < members && go == 0; ++k) {
           const int m = (start + k) % members;
-          const int d = ld_acquire(done + m);
+          const int d = *reinterpret_cast<const volatile int*>(done + m);
           if (d >= mops[m]) continue;
           const int j = mop0[m] + d;
           const int end = (int)ops[j].tile0 + ops[j].ntiles;
@@ -140,11 +142,14 @@ __global__ void __launch_bounds__(kPersistThreads)
               atomicOr(&st->err, 1u);
               go = -1;
             } else {
-              __nanosleep(256);
+              __nanosleep(backoff);
+              backoff = backoff < 2048 ? 2 * backoff : 2048;
             }
           }
         } else {
+          fence_acquire();
           idle_since = 0;
+          backoff = 32;
         }
       }
       s_go = go;

@@ -103,34 +103,56 @@ __global__ void __launch_bounds__(kPersistThreads)
   unsigned backoff = 32;
   int start = (int)(blockIdx.x % (unsigned)members);
   for (;;) {
-    if (threadIdx.x == 0) {
-      int go = 0, jo = 0, lt = 0;
-      if (ld_volatile(&st->err) != 0u) {
-        go = -1;
-      } else {
-        // the first member (scanning from this block's rotating start) whose open
-        // operation still has items: take one with a compare-and-swap.  The scan reads
-        // the chain counters with plain volatile loads (an acquire load would invalidate
-        // the SM's L1 for every member looked at); the item taken is then ordered after
-        // the release that opened it by one acquire fence.
-        for (int k = 0; k < members && go == 0; ++k) {
-          const int m = (start + k) % members;
+    if (threadIdx.x < 32) {
+      // warp 0 scans 32 members at a time (from this block's rotating start) for open
+      // operations with items left; the candidate lanes then try, lowest first, to take
+      // one with a compare-and-swap on their chain's item counter.  The scan reads the
+      // counters with plain volatile loads (an acquire load per member would invalidate
+      // the SM's L1); the item taken is ordered after the release that opened it by one
+      // acquire fence.
+      const int lane = threadIdx.x;
+      // one read of the error word, the same for every lane (the loop below and its
+      // warp-wide ballots and shuffles must be uniform)
+      int go = __shfl_sync(0xffffffffu, lane == 0 && ld_volatile(&st->err) != 0u ? -1 : 0, 0);
+      int jo = 0, lt = 0;
+      for (int base = 0; base < members && go == 0; base += 32) {
+        const int k = base + lane;
+        int m = 0, j = 0, end = 0, t = 0;
+        bool cand = false;
+        if (k < members) {
+          m = (start + k) % members;
           const int d = *reinterpret_cast<const volatile int*>(done + m);
-          if (d >= mops[m]) continue;
-          const int j = mop0[m] + d;
-          const int end = (int)ops[j].tile0 + ops[j].ntiles;
-          int t = *reinterpret_cast<volatile int*>(taken + m);
-          while (t < end) {
-            const int old = atomicCAS(taken + m, t, t + 1);
-            if (old == t) {
-              go = 1;
-              jo = j;
-              lt = t - (int)ops[j].tile0;
-              break;
-            }
-            t = old;
+          if (d < mops[m]) {
+            j = mop0[m] + d;
+            end = (int)ops[j].tile0 + ops[j].ntiles;
+            t = *reinterpret_cast<const volatile int*>(taken + m);
+            cand = t < end;
           }
         }
+        unsigned mask = __ballot_sync(0xffffffffu, cand);
+        while (mask != 0u && go == 0) {
+          const int src = __ffs(mask) - 1;
+          int got = 0, glt = 0;
+          if (lane == src) {
+            while (t < end) {
+              const int old = atomicCAS(taken + m, t, t + 1);
+              if (old == t) {
+                got = 1;
+                glt = t - (int)ops[j].tile0;
+                break;
+              }
+              t = old;
+            }
+          }
+          if (__shfl_sync(0xffffffffu, got, src)) {
+            go = 1;
+            jo = __shfl_sync(0xffffffffu, j, src);
+            lt = __shfl_sync(0xffffffffu, glt, src);
+          }
+          mask &= mask - 1u;
+        }
+      }
+      if (lane == 0) {
         start = (start + 1) % members;
         if (go == 0) {
           if (ld_volatile(&st->finished) >= (unsigned)active) {
@@ -146,15 +168,16 @@ __global__ void __launch_bounds__(kPersistThreads)
               backoff = backoff < 2048 ? 2 * backoff : 2048;
             }
           }
-        } else {
+        } else if (go > 0) {
           fence_acquire();
           idle_since = 0;
           backoff = 32;
         }
+        s_go = go;
+        s_op = jo;
+        s_lt = lt;
       }
-      s_go = go;
-      s_op = jo;
-      s_lt = lt;
+      start = __shfl_sync(0xffffffffu, start, 0);
     }
     __syncthreads();
     const int go = s_go;

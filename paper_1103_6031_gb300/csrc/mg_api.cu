@@ -1663,8 +1663,8 @@ mg_status batch_graph_persistent(mg_batch* b, const std::vector<int>& active, Ba
   const size_t off_m = align_up(off_f + n * sizeof(unsigned*), 256);   // mop0[n], mops[n]
   const size_t off_s = align_up(off_m + 2 * n * sizeof(int), 256);     // PState
   const size_t off_d = off_s + align_up(sizeof(PState), 16);           // done[n]
-  const size_t off_t = off_d + align_up(n * sizeof(int), 16);          // taken[n]
-  const size_t off_c = off_t + align_up(n * sizeof(int), 16);          // count[ops]
+  const size_t off_t = off_d + align_up(n * sizeof(int), 16);          // taken[ops]
+  const size_t off_c = off_t + align_up(ops.size() * sizeof(int), 16); // count[ops]
   const size_t bytes = off_c + ops.size() * sizeof(int);
   std::vector<unsigned char> host(off_s, 0);
   std::memcpy(host.data(), ops.data(), ops.size() * sizeof(POp));

@@ -4,12 +4,13 @@
 // Each hierarchy's operations form a chain (ops[mop0[m] .. mop0[m] + mops[m]), items
 // numbered along the chain); only the first incomplete operation of a chain is open.
 // A block of 128 threads scans the hierarchies (from a rotating start) for one whose
-// open operation still has items, takes one with a compare-and-swap on that chain's
-// item counter, runs the item's blocks through the same bodies the stream kernels run
+// open operation still has items, takes one, runs the item's blocks through the same bodies the stream kernels run
 // (mg_vbody.cuh, with plain loads, since items read what earlier items of the launch
 // wrote), and counts it done; the block that completes an operation's last item opens
 // the next one by publishing the chain's done counter with release semantics (a taker
-// orders its item after that release with an acquire fence).  A block never waits on an item it holds, so every
+// orders its item after that release with an acquire fence).  Items are tickets from
+// the operation's own counter, so a ticket drawn late (past the operation's items) is
+// dropped without retries.  A block never waits on an item it holds, so every
 // taken item completes; a block that finds nothing open waits, and a wait longer than
 // wait_ns without a single item (a defect: no chain can advance) sets the error word,
 // after which every block stops.
@@ -106,7 +107,9 @@ __global__ void __launch_bounds__(kPersistThreads)
     if (threadIdx.x < 32) {
       // warp 0 scans 32 members at a time (from this block's rotating start) for open
       // operations with items left; the candidate lanes then try, lowest first, to take
-      // one with a compare-and-swap on their chain's item counter.  The scan reads the
+      // one: a ticket from the operation's own item counter (atomicAdd; a ticket past
+      // the operation's items is simply dropped, and the counter is never reused, so
+      // there are no compare-and-swap retries under contention).  The scan reads the
       // counters with plain volatile loads (an acquire load per member would invalidate
       // the SM's L1); the item taken is ordered after the release that opened it by one
       // acquire fence.
@@ -117,16 +120,15 @@ __global__ void __launch_bounds__(kPersistThreads)
       int jo = 0, lt = 0;
       for (int base = 0; base < members && go == 0; base += 32) {
         const int k = base + lane;
-        int m = 0, j = 0, end = 0, t = 0;
+        int j = 0, nt = 0;
         bool cand = false;
         if (k < members) {
-          m = (start + k) % members;
+          const int m = (start + k) % members;
           const int d = *reinterpret_cast<const volatile int*>(done + m);
           if (d < mops[m]) {
             j = mop0[m] + d;
-            end = (int)ops[j].tile0 + ops[j].ntiles;
-            t = *reinterpret_cast<const volatile int*>(taken + m);
-            cand = t < end;
+            nt = ops[j].ntiles;
+            cand = *reinterpret_cast<const volatile int*>(taken + j) < nt;
           }
         }
         unsigned mask = __ballot_sync(0xffffffffu, cand);
@@ -134,14 +136,10 @@ __global__ void __launch_bounds__(kPersistThreads)
           const int src = __ffs(mask) - 1;
           int got = 0, glt = 0;
           if (lane == src) {
-            while (t < end) {
-              const int old = atomicCAS(taken + m, t, t + 1);
-              if (old == t) {
-                got = 1;
-                glt = t - (int)ops[j].tile0;
-                break;
-              }
-              t = old;
+            const int t = atomicAdd(taken + j, 1);
+            if (t < nt) {
+              got = 1;
+              glt = t;
             }
           }
           if (__shfl_sync(0xffffffffu, got, src)) {
@@ -262,7 +260,7 @@ extern "C" mg_status mg_selftest_persist_wait(void) {
   const size_t off_w = up(2 * sizeof(POp));
   const size_t off_z = up(off_w + persist_weight_bytes());
   const size_t off_s = up(off_z + 1024 * sizeof(float));
-  const size_t off_d = up(off_s + sizeof(PState));  // done[2], taken[2], count[2]
+  const size_t off_d = up(off_s + sizeof(PState));  // done[2], taken[2 ops], count[2 ops]
   const size_t off_c = up(off_d + 6 * sizeof(int));  // mop0[2], mops[2]
   const size_t bytes = off_c + 4 * sizeof(int);
   char* d = nullptr;

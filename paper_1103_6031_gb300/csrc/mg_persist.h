@@ -62,8 +62,8 @@ struct PState {
 // in the chain and tile0 = the chain-local number of the operation's first item);
 // members: entries of mop0/mops (a member not in this launch has mops = 0); active:
 // members with work; wts[member]: float weights; per member done[] (completed
-// operations) and taken[] (items taken), per operation count[] (items completed), all
-// zero at launch.  wait_ns bounds the time a block may find nothing to take; running
+// operations), per operation taken[] (item tickets handed out) and count[] (items
+// completed), all zero at launch.  wait_ns bounds the time a block may find nothing to take; running
 // out sets st->err and every block stops.
 cudaError_t launch_persist(const POp* ops, const int* mop0, const int* mops, int members,
                            int active, const void* wts, PState* st, int* done, int* taken,

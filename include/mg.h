@@ -90,14 +90,17 @@ typedef enum { MG_FP64 = 0, MG_MIXED = 1 } mg_precision;
  * host loop, so no host round trip separates two iterations.  Same launches and
  * results as the host loop; ignored with MG_FLAG_NO_GRAPHS or while profiling. */
 #define MG_FLAG_DEVICE_LOOP 16
-/* MG_FLAG_PERSISTENT: in mg_batch_lpt_pipeline, when every member is MG_MIXED and sets
- * this flag, the float32 half of each outer iteration of all active members (zero
- * correction, inner V-cycles) runs as ONE persistent kernel launch over a work list of
- * (hierarchy, level operation, block range) items, instead of one launch per level
- * operation per member: blocks take items in chain order and wait, bounded by 2 s, for
- * their hierarchy's earlier operations (a wait that runs out gives MG_ETIMEOUT).  The
- * float64 half (update, ghosts, residual norm) follows on the members' own streams.
- * Results are bit-identical to the per-operation launches.  Ignored outside a batch. */
+/* MG_FLAG_PERSISTENT: in mg_batch_lpt_pipeline, the float32 half of each outer
+ * iteration (zero correction, inner V-cycles) of every active MG_MIXED member that sets
+ * this flag runs inside ONE persistent kernel launch over a work list of (hierarchy,
+ * level operation, block range) items, instead of one launch per level operation per
+ * member: each hierarchy's operations form a chain, and a block takes an item only from
+ * a chain whose earlier operations have completed (so no block waits on an item it
+ * holds); a block that finds nothing to take for 2 s (a defect) stops the launch with
+ * MG_ETIMEOUT.  The float64 half (update, ghosts, residual norm) follows on the members'
+ * own streams; members without the flag run their per-operation launches concurrently
+ * with the persistent launch.  Results are bit-identical to the per-operation launches.
+ * Ignored outside a batch. */
 #define MG_FLAG_PERSISTENT 32
 
 typedef struct {
@@ -264,6 +267,12 @@ mg_status mg_batch_lpt_pipeline(mg_batch* b, int host_buffers, const double* con
 
 /* Message for the last failing batch call ("" if none; NULL-safe). */
 const char* mg_batch_last_error(const mg_batch* b);
+
+/* Grid of the persistent launch (MG_FLAG_PERSISTENT members): blocks_per_sm blocks per
+ * SM (1..64, capped at what fits), or 0 (default) for as many as fit, which leaves no
+ * room for the concurrent per-operation launches of members without the flag.  Drops
+ * the batch's cached graphs.  Errors: MG_EINVAL. */
+mg_status mg_batch_set_persistent_blocks(mg_batch* b, int blocks_per_sm);
 
 /* Serving runtime: a request queue in front of resident hierarchies, driven by
  * one native scheduler thread.  A request is mg_lpt_pipeline(host_buffers = 1)

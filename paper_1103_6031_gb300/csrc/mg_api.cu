@@ -1581,6 +1581,7 @@ struct mg_batch {
   std::vector<cudaEvent_t> ready;  // member stream -> batch stream ordering before a replay
   // per set of active members and their bodies: 0 inactive, else 1 + inner cycles
   std::map<std::vector<int>, BatchGraph> graphs;
+  int persist_blocks_per_sm = 0;  // persistent launch: blocks per SM (0: as many as fit)
   std::string err;
 };
 
@@ -1605,28 +1606,37 @@ mg_status member_status(mg_batch* b, int i, mg_status st) {
   return st;
 }
 
-// Every member is MG_MIXED with MG_FLAG_PERSISTENT (and no device-side loop): the
-// float32 halves of their outer iterations run as one persistent launch.
-bool batch_persistent(const mg_batch* b) {
-  for (const mg_hierarchy* h : b->m)
-    if (!h->mixed || !(h->cfg.flags & MG_FLAG_PERSISTENT) || (h->cfg.flags & MG_FLAG_NO_GRAPHS))
-      return false;
-  return true;
+// A member whose float32 V-cycles join the persistent launch: MG_MIXED with
+// MG_FLAG_PERSISTENT and graphs on.
+bool member_persistent(const mg_hierarchy* h) {
+  return h->mixed && (h->cfg.flags & MG_FLAG_PERSISTENT) && !(h->cfg.flags & MG_FLAG_NO_GRAPHS);
+}
+
+bool batch_persistent(const mg_batch* b, const std::vector<int>& active) {
+  for (size_t i = 0; i < b->m.size(); ++i)
+    if (active[i] && member_persistent(b->m[i])) return true;
+  return false;
 }
 
 constexpr unsigned long long kPersistWaitNs = 2000000000ull;  // 2 s per dependency wait
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-// Persistent mode: the active members' float32 halves are recorded as work lists (the
-// members' host state advances as for a capture), uploaded, and captured as [reset
-// state, persistent launch, wait flags] followed by each member's float64 half on its
-// own stream.
+// Persistent mode: the float32 halves of the active members that set MG_FLAG_PERSISTENT
+// are recorded as work lists (the members' host state advances as for a capture),
+// uploaded, and captured as [reset state, persistent launch, wait flags] followed by
+// each such member's float64 half on its own stream; the other active members' whole
+// iterations are captured as branches that run concurrently with the persistent launch.
 mg_status batch_graph_persistent(mg_batch* b, const std::vector<int>& active, BatchGraph& g) {
   const size_t n = b->m.size();
+  std::vector<int> pers(n, 0), plain(n, 0);
+  for (size_t i = 0; i < n; ++i) {
+    pers[i] = active[i] && member_persistent(b->m[i]);
+    plain[i] = active[i] && !pers[i];
+  }
   std::vector<std::vector<POp>> lists(n);
   for (size_t i = 0; i < n; ++i) {
-    if (!active[i]) continue;
+    if (!pers[i]) continue;
     mg_hierarchy* h = b->m[i];
     h->rec = &lists[i];
     const mg_status st = mixed_inner(h);
@@ -1641,7 +1651,7 @@ mg_status batch_graph_persistent(mg_batch* b, const std::vector<int>& active, Ba
   int active_n = 0;
   for (size_t i = 0; i < n; ++i) {
     mop0[i] = (int)ops.size();
-    if (!active[i]) continue;
+    if (!pers[i]) continue;
     ++active_n;
     long long t = 0;
     for (size_t q = 0; q < lists[i].size(); ++q) {
@@ -1671,13 +1681,19 @@ mg_status batch_graph_persistent(mg_batch* b, const std::vector<int>& active, Ba
   std::vector<unsigned*> flags(n, nullptr);
   for (size_t i = 0; i < n; ++i) {
     persist_weights(b->m[i]->w, host.data() + off_w + i * wb);
-    flags[i] = active[i] ? b->m[i]->wait_err : nullptr;
+    flags[i] = pers[i] ? b->m[i]->wait_err : nullptr;
   }
   std::memcpy(host.data() + off_f, flags.data(), n * sizeof(unsigned*));
   std::memcpy(host.data() + off_m, mop0.data(), n * sizeof(int));
   std::memcpy(host.data() + off_m + n * sizeof(int), mops.data(), n * sizeof(int));
   int grid = 0;
   BCK(persist_grid(&grid));
+  if (b->persist_blocks_per_sm > 0) {
+    int dev = 0, sms = 0;
+    BCK(cudaGetDevice(&dev));
+    BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    grid = std::min(grid, sms * b->persist_blocks_per_sm);
+  }
   char* d = nullptr;
   BCK(cudaMalloc(&d, bytes));
   g.dbuf = d;
@@ -1692,15 +1708,37 @@ mg_status batch_graph_persistent(mg_batch* b, const std::vector<int>& active, Ba
 
   BCK(cudaStreamBeginCapture(b->s, cudaStreamCaptureModeRelaxed));
   mg_status rs = MG_OK;
-  cudaError_t e = cudaMemsetAsync(d + off_s, 0, bytes - off_s, b->s);
+  cudaError_t e = cudaSuccess;
+  // the members outside the persistent launch: their whole iterations as branches
+  bool any_plain = false;
+  for (size_t i = 0; i < n; ++i) any_plain = any_plain || plain[i];
+  if (any_plain) e = cudaEventRecord(b->fork, b->s);
+  for (size_t i = 0; i < n && rs == MG_OK && e == cudaSuccess; ++i) {
+    if (!plain[i]) continue;
+    mg_hierarchy* h = b->m[i];
+    e = cudaStreamWaitEvent(h->s, b->fork, 0);
+    if (e != cudaSuccess) break;
+    const mg_stats snap = h->stats;
+    const unsigned keep = h->active_mask;
+    h->active_mask = 0;
+    rs = solve_body(h);
+    h->active_mask = keep;
+    for (int f = 0; f < MG_K_FAMILIES; ++f) {
+      g.delta[i].launches[f] = h->stats.launches[f] - snap.launches[f];
+      g.delta[i].cells[f] = h->stats.cells[f] - snap.cells[f];
+    }
+    h->stats = snap;
+    if (rs != MG_OK) member_status(b, (int)i, rs);
+  }
+  if (e == cudaSuccess && rs == MG_OK) e = cudaMemsetAsync(d + off_s, 0, bytes - off_s, b->s);
   if (e == cudaSuccess)
     e = launch_persist(reinterpret_cast<const POp*>(d), dmop0, dmop0 + n, (int)n, active_n,
                        d + off_w, st, done, taken, count, kPersistWaitNs, grid, b->s);
   if (e == cudaSuccess)
     e = launch_persist_flags(st, reinterpret_cast<unsigned* const*>(d + off_f), (int)n, b->s);
-  if (e == cudaSuccess) e = cudaEventRecord(b->fork, b->s);
+  if (e == cudaSuccess && rs == MG_OK) e = cudaEventRecord(b->fork, b->s);
   for (size_t i = 0; i < n && rs == MG_OK && e == cudaSuccess; ++i) {
-    if (!active[i]) continue;
+    if (!pers[i]) continue;
     mg_hierarchy* h = b->m[i];
     e = cudaStreamWaitEvent(h->s, b->fork, 0);
     if (e != cudaSuccess) break;
@@ -1719,6 +1757,11 @@ mg_status batch_graph_persistent(mg_batch* b, const std::vector<int>& active, Ba
       break;
     }
     e = cudaEventRecord(b->join[i], h->s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->s, b->join[i], 0);
+  }
+  for (size_t i = 0; i < n && rs == MG_OK && e == cudaSuccess; ++i) {
+    if (!plain[i]) continue;
+    e = cudaEventRecord(b->join[i], b->m[i]->s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->s, b->join[i], 0);
   }
   cudaGraph_t graph = nullptr;
@@ -1740,7 +1783,7 @@ mg_status batch_graph(mg_batch* b, const std::vector<int>& active, BatchGraph** 
     *out = &it->second;
     return MG_OK;
   }
-  if (batch_persistent(b)) {
+  if (batch_persistent(b, active)) {
     BatchGraph g;
     g.delta.resize(b->m.size());
     const mg_status st = batch_graph_persistent(b, active, g);
@@ -2198,6 +2241,20 @@ mg_status mg_batch_destroy(mg_batch* b) {
 }
 
 const char* mg_batch_last_error(const mg_batch* b) { return b ? b->err.c_str() : ""; }
+
+mg_status mg_batch_set_persistent_blocks(mg_batch* b, int blocks_per_sm) {
+  if (!b || blocks_per_sm < 0 || blocks_per_sm > 64) return MG_EINVAL;
+  if (b->persist_blocks_per_sm != blocks_per_sm) {
+    if (b->s) cudaStreamSynchronize(b->s);
+    for (auto& kv : b->graphs) {
+      if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+      if (kv.second.dbuf) cudaFree(kv.second.dbuf);
+    }
+    b->graphs.clear();
+    b->persist_blocks_per_sm = blocks_per_sm;
+  }
+  return MG_OK;
+}
 
 mg_status mg_batch_lpt_pipeline(mg_batch* b, int host_buffers, const double* const* const delta[],
                                 double* const* const phi1[], double* const* const phi2[],

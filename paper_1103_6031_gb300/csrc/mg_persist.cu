@@ -95,7 +95,9 @@ __device__ __forceinline__ void run_block(const POp& op, const CfW<float>& w, in
   }
 }
 
-__global__ void __launch_bounds__(kPersistThreads)
+// At least 8 blocks per SM (64 registers): the stencil bodies are latency-bound on L1
+// and need the warps; at 96 registers 5 blocks fit.
+__global__ void __launch_bounds__(kPersistThreads, 8)
     k_persist(const POp* __restrict__ ops, const int* __restrict__ mop0, const int* __restrict__ mops,
               int members, int active, const CfW<float>* __restrict__ wts, PState* st, int* done,
               int* taken, int* count, unsigned long long wait_ns) {
@@ -163,7 +165,7 @@ __global__ void __launch_bounds__(kPersistThreads)
               go = -1;
             } else {
               __nanosleep(backoff);
-              backoff = backoff < 2048 ? 2 * backoff : 2048;
+              backoff = backoff < 512 ? 2 * backoff : 512;
             }
           }
         } else if (go > 0) {

@@ -168,6 +168,7 @@ def load_library(path=None):
         "mg_selftest_wait_limit": (ctypes.c_int, []),
         "mg_fp64_fma_rate": (ctypes.c_int, [ctypes.c_int, vp, ctypes.POINTER(ctypes.c_double)]),
         "mg_selftest_persist_wait": (ctypes.c_int, []),
+        "mg_batch_set_persistent_blocks": (ctypes.c_int, [vp, ctypes.c_int]),
         "mg_hybrid_correction": (ctypes.c_int, [vp, vp, ctypes.POINTER(vp)]),
         "mg_lla_density": (ctypes.c_int, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_double,
                                           ctypes.c_double, ctypes.POINTER(vp)]),
@@ -433,6 +434,13 @@ class Batch:
         if st != 0:
             raise MGError(st, "mg_batch_create")
         self.b = handle
+
+    def set_persistent_blocks(self, blocks_per_sm):
+        """Blocks per SM of the persistent launch of the MG_FLAG_PERSISTENT members (0:
+        as many as fit)."""
+        st = self.lib.mg_batch_set_persistent_blocks(self.b, int(blocks_per_sm))
+        if st != 0:
+            raise MGError(st, "mg_batch_set_persistent_blocks")
 
     def pipeline(self, deltas, outputs=None, host=False, allow_noconv=False):
         """deltas[i]: member i's per-level inputs; returns (outputs, infos1, infos2),

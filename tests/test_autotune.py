@@ -53,3 +53,35 @@ def test_tuned_schedule_converges_and_is_fastest(pkg):
         for x, y in zip(a[key], b[key]):
             err = float(torch.sqrt(((x - y) ** 2).sum() / (y ** 2).sum()))
             assert err <= 1e-6, key
+
+
+def test_joint_tuner_keeps_only_gains_beyond_the_threshold(pkg, monkeypatch):
+    """Coordinate descent on the batch time (a fake timing here): a class's candidate
+    replaces the schedule only when the batch gets faster by more than `gain`, larger
+    classes are visited first, and a faster launch mode is adopted the same way."""
+    from paper_1103_6031_gb300 import autotune
+    geoms = config_batch()[:12]
+    calls = []
+
+    def fake(geoms_, deltas, sched, tol, mode=autotune.LAUNCH_MODES[0], reps=2):
+        calls.append((dict(sched), mode[0]))
+        t = 1.0
+        for c, p in sched.items():
+            if p == (3, 2, 2, 4):
+                t -= 0.05 if c == "l" else 0.005     # a real gain for "l", noise elsewhere
+        if mode[0] == "persistent_xs":
+            t -= 0.2
+        return t
+
+    monkeypatch.setattr(autotune, "time_batch", fake)
+    sched, mode, log = autotune.tune_batch_joint(geoms, None, 1e-8, gain=0.02)
+    classes = {autotune.size_class(g) for g in geoms}
+    assert set(sched) == classes
+    for c in classes:
+        assert sched[c] == ((3, 2, 2, 4) if c == "l" else autotune.DEFAULT_PARAMS), (c, sched)
+    assert mode[0] == "persistent_xs"
+    assert log[0][0] == "default" and len(log) == len(calls)
+    order = [name.split("=")[0] for name, _ in log[1:] if "=" in name and not name.startswith("mode")]
+    work = {c: sum(g.level_cells() for g in geoms if autotune.size_class(g) == c) for c in classes}
+    firsts = list(dict.fromkeys(order))
+    assert firsts == sorted(classes, key=lambda c: -work[c])

@@ -75,12 +75,9 @@ typedef enum { MG_FP64 = 0, MG_MIXED = 1 } mg_precision;
 #define MG_FLAG_NO_GRAPHS 1
 /* Smoother kernel: by default float32 nests of at least 2^23 cells are smoothed
  * by the kernel that stages plane tiles in shared memory with the tensor-memory
- * accelerator; other float32 levels whose sides are multiples of 4 (x), 8 (y) and
- * 64 (z) by a kernel that stages each plane's tile with one vector load per thread
- * and marches 4 planes along x; every other level by the kernel that loads every
- * stencil value from global memory; all give bit-identical results.
- * MG_FLAG_NO_TMA: the last kernel on every level.  MG_FLAG_TMA_ALL: the first
- * kernel on every level. */
+ * accelerator, other levels by the kernel that loads every stencil value from
+ * global memory; both give bit-identical results.  MG_FLAG_NO_TMA: the second
+ * kernel on every level.  MG_FLAG_TMA_ALL: the first kernel on every level. */
 #define MG_FLAG_NO_TMA 2
 #define MG_FLAG_TMA_ALL 4
 /* MG_FLAG_HYBRID: the displacements of mg_lpt_pipeline and mg_batch_lpt_pipeline get

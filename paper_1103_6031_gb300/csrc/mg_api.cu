@@ -697,19 +697,10 @@ mg_status half_sweep(mg_hierarchy* h, int l, int colour) {
     b.cur ^= 1;
     return MG_OK;
   }
-  bool xm = false;
-  if constexpr (std::is_same<T, float>::value)
-    xm = !b.tma && !(h->cfg.flags & MG_FLAG_NO_TMA) && smooth_xm_usable(L.G);
   if (b.tma)
     KL(MG_K_SMOOTH, (cells_of(L.G) + 1) / 2,
        launch_smooth_half_tma<T>(h->cfg.order, L.G, &b.tm[b.cur], &b.tm_f, b.u[1 - b.cur], a_f,
                                  colour, L.periodic ? 1 : 0, h->wait_err, h->s));
-  else if (xm)
-    KL(MG_K_SMOOTH, (cells_of(L.G) + 1) / 2,
-       launch_smooth_half_xm(h->cfg.order, L.G, reinterpret_cast<const float*>(b.u[b.cur]),
-                             reinterpret_cast<float*>(b.u[1 - b.cur]),
-                             reinterpret_cast<const float*>(b.ffas), a_f, colour,
-                             L.periodic ? 1 : 0, h->s));
   else
     KL(MG_K_SMOOTH, (cells_of(L.G) + 1) / 2,
        launch_smooth_half<T>(h->cfg.order, L.G, b.u[b.cur], b.u[1 - b.cur], b.ffas, a_f, colour,

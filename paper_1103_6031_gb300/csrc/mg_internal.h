@@ -102,14 +102,6 @@ bool smooth_tma_usable(const Grid& G);
 // Opt the TMA smoother kernels in to their shared-memory size on the current device.
 cudaError_t prepare_smooth_tma();
 
-// ---- float32 smoother with shared-memory plane tiles and an x-march (mg_smooth_xm.cu) ----
-// Same update and result as launch_smooth_half<float>; usable when n0 % 4 == 0,
-// n1 % 8 == 0, n2 % 64 == 0 (and the make_grid row layout).
-bool smooth_xm_usable(const Grid& G);
-cudaError_t launch_smooth_half_xm(int order, const Grid& G, const float* uin, float* uout,
-                                  const float* f, double a_f, int colour, int periodic,
-                                  cudaStream_t s);
-
 // ---- kernels: ghost zones (mg_ghost.cu) ----
 template <typename T>
 cudaError_t launch_ghost_periodic(const Grid& G, T* u, cudaStream_t s);

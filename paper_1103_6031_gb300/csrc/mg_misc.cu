@@ -73,9 +73,9 @@ constexpr int kRedBlock = 256;
 
 // One block per (x plane, 8 y rows); 32 lanes stride along z.  Block b writes
 // its partial sums to slot b, so the reduction order is fixed.
-// With r32 != nullptr the float64 residual of every interior cell is also
-// stored, rounded to float32, as the source of the correction equation
-// (mixed precision); the sums still skip covered cells.
+// With r32 != nullptr the float64 residual of every uncovered interior cell is also
+// stored, rounded to float32, as the source of the correction equation (mixed
+// precision); covered cells are skipped for both.
 template <int ORDER>
 __global__ void __launch_bounds__(kRedBlock)
     k_norm_partial(Grid G, const double* __restrict__ u, const double* __restrict__ f,
@@ -90,13 +90,14 @@ __global__ void __launch_bounds__(kRedBlock)
     const bool row_cov = i >= clo.x && i < chi.x && j >= clo.y && j < chi.y;
     const long long row = gidx(G, i, j, 0);
     for (int k = lane; k < G.n2; k += 32) {
+      // covered cells: no norm term, and no correction source either (the FAS
+      // restriction overwrites a covered parent cell's source before the parent uses it)
       const bool cov = row_cov && k >= clo.z && k < chi.z;
-      if (cov && !r32) continue;
+      if (cov) continue;
       const long long p = row + k;
       const double fv = __ldg(f + p);
       const double r = u ? fma(-invh2, lap_h2<ORDER, double>(u, p, sy, sx), fv) : fv;
       if (r32) r32[p] = (float)r;
-      if (cov) continue;
       rr = fma(r, r, rr);
       ff = fma(fv, fv, ff);
     }

@@ -1084,7 +1084,7 @@ def main(argv=None):
     ap.add_argument("--serve-seconds", type=float, default=5.0,
                     help="seconds of open-loop arrivals in the serving measurement (0: none)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="mean arrivals per second")
-    ap.add_argument("--serve-workers", type=int, default=48, help="concurrent requests at most")
+    ap.add_argument("--serve-workers", type=int, default=96, help="concurrent requests at most")
     ap.add_argument("--serve-impl", choices=["native", "python"], default="native",
                     help="serving runtime: the C++ scheduler (mg_server_*) or Python threads")
     ap.add_argument("--serve-large-side", type=int, default=128,

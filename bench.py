@@ -882,6 +882,16 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    # open-loop serving first, in a fresh process: measured after the other sections
+    # (hundreds of hierarchies made and destroyed, graphs cached), its p50 latency was
+    # 6-15x worse than in a fresh process
+    serving = None
+    if pre is not None and args.serve_seconds > 0 and world == 1:
+        serving = serving_measure(pkg, pre[0], pre[1], pre[2], args.serve_seconds,
+                                  args.serve_rate, args.serve_workers,
+                                  native=args.serve_impl == "native")
+        torch.cuda.empty_cache()
+
     peak_fma, peak_clocks = fp64_peak(pkg, device) if not args.profile_run else (None, None)
     R = solve_workload(pkg, name, deltas_np, args.steps, args.warmup, device, flush, barrier, dist,
                        geom=geom, mixed_too=not args.profile_run, profile_run=args.profile_run,
@@ -912,15 +922,6 @@ def run_ours(args):
     all_gops = SMOOTH_OPS_PER_UPDATE[geom.order] * all_updates / (all_ms * 1e-3) / 1e9
     est = {k: v["event_ms"] / max(v["timed"], 1) * v["launches"] for k, v in fam.items() if v["timed"]}
     share_kernel_time = est.get("smooth", 0.0) / max(sum(est.values()), 1e-12)
-
-    # open-loop serving, measured early in the process: measured after the batched
-    # and autotuning sections (hundreds of hierarchies made and destroyed), its p50
-    # latency was 15x worse than in a fresh process
-    serving = None
-    if pre is not None and args.serve_seconds > 0 and world == 1:
-        serving = serving_measure(pkg, pre[0], pre[1], pre[2], args.serve_seconds,
-                                  args.serve_rate, args.serve_workers,
-                                  native=args.serve_impl == "native")
 
     # zoom2 beside the deep-zoom headline
     zoom2 = None

@@ -467,6 +467,9 @@ def serving_measure(pkg, geoms, deltas_np, large, seconds, rate, workers, native
     reqs, cells = draw(n, rng)
     if native:
         server = serve.NativeServer(max_active=workers, hbm_budget=64 << 30, keep_outputs=False)
+        # pinned output sets of the large class up front (0.5-4 GB each); the others
+        # come from the warm-up below and are recycled from then on
+        server.reserve_outputs(cfg_large, 4)
     else:
         server = serve.Server(workers=workers, hbm_budget=64 << 30, keep_outputs=False)
     # warm server: one untimed request per configuration first, so that the timed

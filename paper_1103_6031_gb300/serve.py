@@ -250,6 +250,10 @@ class NativeServer:
         self._next_id = 0
         self._stop = False
         self._clock_ok = _monotonic_perf_counter()
+        # pinned output sets by leaf shapes, returned here when results are not kept:
+        # allocating pinned host memory (cudaHostAlloc; 0.5 GB for a 128^3 + 3 x 128^3
+        # request) in the submitting thread delayed the arrivals behind it
+        self._pool = collections.defaultdict(list)
         self._poller = threading.Thread(target=self._poll_loop, daemon=True)
         self._poller.start()
 
@@ -263,10 +267,11 @@ class NativeServer:
         if nbytes > self.hbm_budget:
             raise mg.MGError(2, "request needs %d bytes, above the HBM budget" % nbytes)
         shapes = _leaf_shapes(req.cfg)
-        pin = lambda s: self._torch.empty(s, dtype=self._torch.float64, pin_memory=True)
-        out = {"phi1": [pin(s) for s in shapes], "phi2": [pin(s) for s in shapes],
-               "disp1": [pin(s) for s in shapes for _ in range(3)],
-               "disp2": [pin(s) for s in shapes for _ in range(3)]}
+        with self.lock:
+            pooled = self._pool[tuple(shapes)]
+            out = pooled.pop() if pooled else None
+        if out is None:
+            out = self.output_set(shapes)
         d3 = [s for s in shapes for _ in range(3)]
         arrays = [mg._ptrs(req.deltas, shapes, True), mg._ptrs(out["phi1"], shapes, True),
                   mg._ptrs(out["phi2"], shapes, True), mg._ptrs(out["disp1"], d3, True),
@@ -282,6 +287,22 @@ class NativeServer:
             with self.lock:
                 del self.inflight[rid]
             raise mg.MGError(st, "mg_server_submit")
+
+    def output_set(self, shapes):
+        """A set of pinned host outputs (phi1, phi2, disp1, disp2) for leaf shapes."""
+        pin = lambda s: self._torch.empty(s, dtype=self._torch.float64, pin_memory=True)
+        return {"phi1": [pin(s) for s in shapes], "phi2": [pin(s) for s in shapes],
+                "disp1": [pin(s) for s in shapes for _ in range(3)],
+                "disp2": [pin(s) for s in shapes for _ in range(3)]}
+
+    def reserve_outputs(self, cfg, count):
+        """Pre-allocates `count` pooled output sets for requests of configuration cfg
+        (used when results are not kept), so that arrivals never wait for pinned
+        allocation."""
+        shapes = tuple(_leaf_shapes(cfg))
+        sets = [self.output_set(shapes) for _ in range(count)]
+        with self.lock:
+            self._pool[shapes].extend(sets)
 
     def _poll_loop(self):
         buf = (mg.MGServerResult * 64)()
@@ -303,7 +324,11 @@ class NativeServer:
                     if r.status != 0:
                         req.error = mg.MGError(r.status, "request %d: %s"
                                                % (req.id, r.error.decode(errors="replace")))
-                    req.outputs = out if self.keep_outputs else None
+                    if self.keep_outputs:
+                        req.outputs = out
+                    else:
+                        req.outputs = None
+                        self._pool[tuple(_leaf_shapes(req.cfg))].append(out)
                     self.completed.append(req)
                 self.lock.notify_all()
 

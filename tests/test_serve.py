@@ -264,3 +264,36 @@ def test_native_server_rejects_invalid_and_oversized_requests():
     assert server.drain(timeout=60)
     server.close()
     assert r.error is None and r.info[0]["rel_residual"] <= 1e-9
+
+
+@pytest.mark.gpu
+def test_native_server_recycles_output_sets_when_results_are_dropped():
+    """With keep_outputs=False a finished request's pinned output set goes back to a
+    pool and the next request of the same shapes reuses it (no pinned allocation in
+    the submitting thread); a request kept after that still gets correct results."""
+    torch, pkg = _native_setup()
+    from paper_1103_6031_gb300.serve import NativeServer, Request
+    geom, _ = GEOMS[1]
+    cfg = pkg.config_from_geometry(geom, tol=1e-9, max_cycles=40)
+    inputs = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in make_delta(geom, 5)]
+    server = NativeServer(max_active=2, hbm_budget=8 << 30, keep_outputs=False)
+    server.reserve_outputs(cfg, 1)
+    key = next(iter(server._pool))
+    first = server._pool[key][-1]
+    r = Request(0, cfg, inputs)
+    server.submit(r)
+    assert len(server._pool[key]) == 0          # the reserved set is in use
+    server.drain()
+    assert r.error is None and r.outputs is None
+    assert len(server._pool[key]) == 1 and server._pool[key][0] is first
+    server.keep_outputs = True
+    r2 = Request(1, cfg, inputs)
+    server.submit(r2)
+    server.drain()
+    server.close()
+    alone = pkg.Hierarchy(cfg)
+    want, _, _ = alone.pipeline(inputs, host=True)
+    alone.close()
+    for k in ("phi1", "phi2", "disp1", "disp2"):
+        for a, b in zip(r2.outputs[k], want[k]):
+            assert torch.equal(a, b), k

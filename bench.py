@@ -467,9 +467,9 @@ def serving_measure(pkg, geoms, deltas_np, large, seconds, rate, workers, native
     reqs, cells = draw(n, rng)
     if native:
         server = serve.NativeServer(max_active=workers, hbm_budget=64 << 30, keep_outputs=False)
-        # pinned output sets of the large class up front (0.5-4 GB each); the others
-        # come from the warm-up below and are recycled from then on
-        server.reserve_outputs(cfg_large, 4)
+        # pinned output sets of the large class up front (0.5 GB each at 128^3, 4.3 GB at
+        # 256^3); the others come from the warm-up below and are recycled from then on
+        server.reserve_outputs(cfg_large, 8 if large[0].level_cells() < (1 << 24) else 2)
     else:
         server = serve.Server(workers=workers, hbm_budget=64 << 30, keep_outputs=False)
     # warm server: one untimed request per configuration first, so that the timed
@@ -490,6 +490,26 @@ def serving_measure(pkg, geoms, deltas_np, large, seconds, rate, workers, native
     server.completed.clear()
     wall = serve.run_open_loop(server, reqs, rate, seed=SERVE_SEED)
     errors = [r for r in reqs if r.error is not None]
+    # capacity: a closed loop over the same mix (other seed) that keeps `workers`
+    # requests in the server, completions per second until the last result; utilisation
+    # = offered work / that capacity (at ~0.9 and above, queueing makes p50/p99 vary from
+    # run to run)
+    capacity, util = None, None
+    if native:
+        burst, bcells = draw(int(1.5 * rate), np.random.Generator(np.random.PCG64(SERVE_SEED + 2)),
+                             10 * n)
+        t_b = time.perf_counter()
+        for r in burst:
+            while len(server.inflight) >= workers:
+                time.sleep(2e-4)
+            r.arrival = time.perf_counter()
+            server.submit(r)
+        server.drain()
+        wall_b = max(r.done for r in burst) - t_b
+        capacity = {"requests_per_s": sig(len(burst) / wall_b),
+                    "level_cells_per_s": sig(bcells / wall_b), "requests": len(burst),
+                    "in_server": workers}
+        util = sig((cells / seconds) / (bcells / wall_b), 3)
     if native:
         st = server.stats()
         peak_gb, evictions = st["peak_bytes"] / 2 ** 30, st["evictions"]
@@ -507,6 +527,8 @@ def serving_measure(pkg, geoms, deltas_np, large, seconds, rate, workers, native
     out = {"offered_rate_per_s": rate, "requests": n, "seconds_of_arrivals": seconds,
            "completed_per_s": sig(n / wall), "level_cells_per_s": sig(cells / wall),
            "offered_level_cells_per_s": sig(cells / seconds),
+           "capacity": capacity,
+           "utilisation": util,
            "latency_ms": {"p50": sig(stats["p50_ms"]), "p99": sig(stats["p99_ms"]),
                           "mean": sig(stats["mean_ms"]), "max": sig(stats["max_ms"])},
            "queue_wait_ms_p50": sig(1e3 * statistics.median(queue)) if queue else None,
@@ -1060,6 +1082,8 @@ def run_ours(args):
                                "done_per_s": serving["completed_per_s"],
                                "p50_ms": serving["latency_ms"]["p50"],
                                "p99_ms": serving["latency_ms"]["p99"],
+                               "capacity_per_s": (serving["capacity"] or {}).get("requests_per_s"),
+                               "utilisation": serving["utilisation"],
                                "large": serving["mix"].split(" base")[0].split("10% ")[-1],
                                "errors": serving["errors"]}
         print(json.dumps(line))

@@ -252,8 +252,13 @@ class NativeServer:
         self._clock_ok = _monotonic_perf_counter()
         # pinned output sets by leaf shapes, returned here when results are not kept:
         # allocating pinned host memory (cudaHostAlloc; 0.5 GB for a 128^3 + 3 x 128^3
-        # request) in the submitting thread delayed the arrivals behind it
+        # request) in the submitting thread delayed the arrivals behind it.  _owned: every
+        # set allocated per shapes; once a shape has `dropped_sets` of them, a request
+        # whose results are dropped writes into one that may still be in use by another
+        # such request (the copies still run in full; nobody reads the values)
         self._pool = collections.defaultdict(list)
+        self._owned = collections.defaultdict(list)
+        self.dropped_sets = 2
         self._poller = threading.Thread(target=self._poll_loop, daemon=True)
         self._poller.start()
 
@@ -267,11 +272,21 @@ class NativeServer:
         if nbytes > self.hbm_budget:
             raise mg.MGError(2, "request needs %d bytes, above the HBM budget" % nbytes)
         shapes = _leaf_shapes(req.cfg)
+        key = tuple(shapes)
         with self.lock:
-            pooled = self._pool[tuple(shapes)]
+            pooled = self._pool[key]
+            owned = self._owned[key]
             out = pooled.pop() if pooled else None
+            if out is None and not self.keep_outputs and len(owned) >= self.dropped_sets:
+                out = owned[self._next_id % len(owned)]
+                shared = True
+            else:
+                shared = False
         if out is None:
             out = self.output_set(shapes)
+            if not self.keep_outputs:   # kept results belong to the caller
+                with self.lock:
+                    owned.append(out)
         d3 = [s for s in shapes for _ in range(3)]
         arrays = [mg._ptrs(req.deltas, shapes, True), mg._ptrs(out["phi1"], shapes, True),
                   mg._ptrs(out["phi2"], shapes, True), mg._ptrs(out["disp1"], d3, True),
@@ -280,7 +295,7 @@ class NativeServer:
         with self.lock:
             rid = self._next_id
             self._next_id += 1
-            self.inflight[rid] = (req, out, arrays, req.cfg)
+            self.inflight[rid] = (req, None if shared else out, arrays, req.cfg)
             self.peak_inflight = max(self.peak_inflight, len(self.inflight))
         st = self.lib.mg_server_submit(self.h, rid, ct.byref(req.cfg), *[cast(a) for a in arrays])
         if st != 0:
@@ -303,6 +318,7 @@ class NativeServer:
         sets = [self.output_set(shapes) for _ in range(count)]
         with self.lock:
             self._pool[shapes].extend(sets)
+            self._owned[shapes].extend(sets)
 
     def _poll_loop(self):
         buf = (mg.MGServerResult * 64)()
@@ -328,7 +344,8 @@ class NativeServer:
                         req.outputs = out
                     else:
                         req.outputs = None
-                        self._pool[tuple(_leaf_shapes(req.cfg))].append(out)
+                        if out is not None:   # a set this request had to itself
+                            self._pool[tuple(_leaf_shapes(req.cfg))].append(out)
                     self.completed.append(req)
                 self.lock.notify_all()
 

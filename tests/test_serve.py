@@ -297,3 +297,24 @@ def test_native_server_recycles_output_sets_when_results_are_dropped():
     for k in ("phi1", "phi2", "disp1", "disp2"):
         for a, b in zip(r2.outputs[k], want[k]):
             assert torch.equal(a, b), k
+
+
+@pytest.mark.gpu
+def test_native_server_bounds_pinned_sets_for_dropped_results():
+    """Requests whose results are dropped allocate at most `dropped_sets` pinned output
+    sets per shape; more overlapping ones write into a set already in use (nobody reads
+    it), so a burst allocates nothing in the submitting thread and still completes."""
+    torch, pkg = _native_setup()
+    from paper_1103_6031_gb300.serve import NativeServer, Request
+    geom, _ = GEOMS[0]
+    cfg = pkg.config_from_geometry(geom, tol=1e-9, max_cycles=40)
+    inputs = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in make_delta(geom, 6)]
+    server = NativeServer(max_active=8, hbm_budget=8 << 30, keep_outputs=False)
+    reqs = [Request(k, cfg, inputs) for k in range(12)]
+    for r in reqs:
+        server.submit(r)
+    server.drain()
+    key = next(iter(server._owned))
+    assert len(server._owned[key]) == server.dropped_sets
+    assert all(r.error is None and r.done is not None for r in reqs)
+    server.close()

@@ -467,6 +467,10 @@ def serving_measure(pkg, geoms, deltas_np, large, seconds, rate, workers, native
     reqs, cells = draw(n, rng)
     if native:
         server = serve.NativeServer(max_active=workers, hbm_budget=64 << 30, keep_outputs=False)
+        # at most 3 resident hierarchies per configuration: creating one stalls the
+        # device, and uncapped the server kept creating instances under load (20-54 inside
+        # a 5 s window), which cut its capacity by up to half from run to run
+        server.set_max_instances(3)
         # pinned output sets of the large class up front (0.5 GB each at 128^3, 4.3 GB at
         # 256^3); the others come from the warm-up below and are recycled from then on
         server.reserve_outputs(cfg_large, 8 if large[0].level_cells() < (1 << 24) else 2)

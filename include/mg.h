@@ -340,6 +340,14 @@ int mg_server_poll(mg_server* s, mg_server_result* out, int max, double wait_sec
 
 mg_status mg_server_get_stats(mg_server* s, mg_server_stats* out);
 
+/* At most n resident hierarchies per configuration (n = 0, the default: no cap).  A
+ * request whose configuration has n hierarchies, all busy, waits for one of them to
+ * be idle instead of getting a new one: creating a hierarchy (device allocation, and
+ * the capture of its graphs on first use) stalls the device for every running job,
+ * so under load an uncapped server can spend its time making instances.  May be
+ * called at any time; takes effect at the scheduler's next pass. */
+mg_status mg_server_set_max_instances(mg_server* s, int n);
+
 /* Stops taking requests, fails the ones not yet started (status MG_EINVAL,
  * "server closed"), waits for the running ones, frees every hierarchy.
  * NULL-safe.  Results not yet polled are dropped.  No other mg_server_* call on

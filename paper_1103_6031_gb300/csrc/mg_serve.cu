@@ -21,6 +21,7 @@
 #include <time.h>
 
 #include <chrono>
+#include <atomic>
 #include <condition_variable>
 #include <cstdio>
 #include <cstring>
@@ -129,6 +130,7 @@ P* data_or_null(std::vector<P>& v) {
 struct mg_server {
   size_t budget = 0;
   int max_active = 8;
+  std::atomic<int> max_instances{0};  // resident hierarchies per configuration (0: no cap)
   int device = 0;
   std::mutex mu;                    // guards everything below up to `th`
   std::condition_variable cv_work;  // a request was queued, or stop
@@ -265,7 +267,9 @@ void start_on(mg_server* S, Request* r, Slot* sl) {
 // Admission pass; returns whether any request was started or failed.  First every
 // pending request (in arrival order, the first kScan) whose configuration has an
 // idle resident hierarchy starts on it; then, if there is still room, the oldest
-// pending request gets a new hierarchy: at most one creation per pass, so making
+// pending request whose configuration is below the instance cap gets a new
+// hierarchy (the others wait for one of theirs to be idle): at most one creation per
+// pass, so making
 // hierarchies (allocation, and closing idle ones, which waits for the device) never
 // holds up the running jobs for long, and a busy configuration gets a second
 // hierarchy only when its request is the oldest one waiting.
@@ -290,12 +294,28 @@ bool admit(mg_server* S) {
       keep.push_back(r);
     }
   }
-  if (!keep.empty() && (int)S->active.size() < S->max_active) {
-    Request* r = keep.front();
+  // the oldest kept request whose configuration may have one more hierarchy
+  auto creatable = keep.end();
+  for (auto it = keep.begin(); it != keep.end(); ++it) {
+    const int cap = S->max_instances.load(std::memory_order_relaxed);
+    if (cap <= 0) {
+      creatable = it;
+      break;
+    }
+    int n = 0;
+    for (const Slot* sl : S->slots)
+      if (sl->hash == (*it)->hash && sl->key == (*it)->key) ++n;
+    if (n < cap) {
+      creatable = it;
+      break;
+    }
+  }
+  if (creatable != keep.end() && (int)S->active.size() < S->max_active) {
+    Request* r = *creatable;
     Slot* sl = nullptr;
     std::string msg;
     if (create_for(S, r, &sl, &msg)) {
-      keep.pop_front();
+      keep.erase(creatable);
       moved = true;
       if (sl)
         start_on(S, r, sl);
@@ -385,6 +405,12 @@ mg_status mg_server_create(unsigned long long hbm_budget, int max_active, mg_ser
   }
   S->th = std::thread(scheduler, S);
   *out = S;
+  return MG_OK;
+}
+
+mg_status mg_server_set_max_instances(mg_server* S, int n) {
+  if (!S || n < 0) return MG_EINVAL;
+  S->max_instances.store(n, std::memory_order_relaxed);
   return MG_OK;
 }
 

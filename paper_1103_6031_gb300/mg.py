@@ -169,6 +169,7 @@ def load_library(path=None):
         "mg_fp64_fma_rate": (ctypes.c_int, [ctypes.c_int, vp, ctypes.POINTER(ctypes.c_double)]),
         "mg_selftest_persist_wait": (ctypes.c_int, []),
         "mg_batch_set_persistent_blocks": (ctypes.c_int, [vp, ctypes.c_int]),
+        "mg_server_set_max_instances": (ctypes.c_int, [vp, ctypes.c_int]),
         "mg_hybrid_correction": (ctypes.c_int, [vp, vp, ctypes.POINTER(vp)]),
         "mg_lla_density": (ctypes.c_int, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_double,
                                           ctypes.c_double, ctypes.POINTER(vp)]),

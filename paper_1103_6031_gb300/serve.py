@@ -349,6 +349,12 @@ class NativeServer:
                     self.completed.append(req)
                 self.lock.notify_all()
 
+    def set_max_instances(self, n):
+        """At most n resident hierarchies per configuration (0: no cap)."""
+        st = self.lib.mg_server_set_max_instances(self.h, int(n))
+        if st != 0:
+            raise mg.MGError(st, "mg_server_set_max_instances")
+
     def stats(self):
         st = mg.MGServerStats()
         self.lib.mg_server_get_stats(self.h, self._ct.byref(st))

@@ -318,3 +318,32 @@ def test_native_server_bounds_pinned_sets_for_dropped_results():
     assert len(server._owned[key]) == server.dropped_sets
     assert all(r.error is None and r.done is not None for r in reqs)
     server.close()
+
+
+@pytest.mark.gpu
+def test_native_server_instance_cap():
+    """With at most one hierarchy per configuration, overlapping requests of one
+    configuration wait for it instead of getting new ones: one hierarchy is created,
+    and every result equals the solo run bit for bit."""
+    torch, pkg = _native_setup()
+    from paper_1103_6031_gb300.serve import NativeServer, Request
+    geom, _ = GEOMS[1]
+    cfg = pkg.config_from_geometry(geom, tol=1e-9, max_cycles=40)
+    inputs = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in make_delta(geom, 8)]
+    server = NativeServer(max_active=8, hbm_budget=8 << 30)
+    server.set_max_instances(1)
+    reqs = [Request(k, cfg, inputs) for k in range(6)]
+    for r in reqs:
+        server.submit(r)
+    server.drain()
+    st = server.stats()
+    server.close()
+    assert st["created"] == 1 and st["completed"] == 6
+    alone = pkg.Hierarchy(cfg)
+    want, _, _ = alone.pipeline(inputs, host=True)
+    alone.close()
+    for r in reqs:
+        assert r.error is None
+        for k in ("phi1", "phi2", "disp1", "disp2"):
+            for a, b in zip(r.outputs[k], want[k]):
+                assert torch.equal(a, b), (r.id, k)

@@ -43,6 +43,9 @@ UNIT = "level-cells/s"
 # reached 1.0e-6 in float64 and 1.8e-6 in mixed precision)
 SOLVE_TOL = 3e-8
 MIXED_TOL = 1e-8
+# resident hierarchies per configuration in the serving measurement (the warm-up
+# creates them all before the timed window)
+SERVE_INSTANCES = 3
 REF_TOL = 1e-12        # float64 solve the measured errors are taken against
 BATCH_SEED = 1000
 SERVE_SEED = 5
@@ -470,18 +473,21 @@ def serving_measure(pkg, geoms, deltas_np, large, seconds, rate, workers, native
         # at most 3 resident hierarchies per configuration: creating one stalls the
         # device, and uncapped the server kept creating instances under load (20-54 inside
         # a 5 s window), which cut its capacity by up to half from run to run
-        server.set_max_instances(3)
+        server.set_max_instances(SERVE_INSTANCES)
         # pinned output sets of the large class up front (0.5 GB each at 128^3, 4.3 GB at
         # 256^3); the others come from the warm-up below and are recycled from then on
         server.reserve_outputs(cfg_large, 8 if large[0].level_cells() < (1 << 24) else 2)
     else:
         server = serve.Server(workers=workers, hbm_budget=64 << 30, keep_outputs=False)
-    # warm server: one untimed request per configuration first, so that the timed
-    # window sees resident hierarchies with captured graphs (steady state), not the
-    # first-use allocation and capture of 65 configurations
+    # warm server: every configuration served as many times at once as it may have
+    # resident instances (untimed), so that the timed window sees resident hierarchies
+    # with captured graphs (steady state), not the first-use allocation and capture
+    copies = SERVE_INSTANCES if native else 1
     t0 = time.perf_counter()
-    warm = [serve.Request(-1 - i, c, pinned[i]) for i, c in enumerate(cfg_small)]
-    warm.append(serve.Request(-1 - len(cfg_small), cfg_large, large_in))
+    warm = [serve.Request(-1 - copies * i - c, cf, pinned[i])
+            for i, cf in enumerate(cfg_small) for c in range(copies)]
+    warm += [serve.Request(-1 - copies * len(cfg_small) - c, cfg_large, large_in)
+             for c in range(copies)]
     for r in warm:
         server.submit(r)
     server.drain()
@@ -509,7 +515,14 @@ def serving_measure(pkg, geoms, deltas_np, large, seconds, rate, workers, native
     warm_s = time.perf_counter() - t0
     created0 = server.stats()["created"] if native else None
     server.completed.clear()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    st0 = server.stats() if native else None
+    cpu0 = time.process_time()
     wall = serve.run_open_loop(server, reqs, rate, seed=SERVE_SEED)
+    cpu_window = time.process_time() - cpu0
+    st1 = server.stats() if native else None
+    clocks = sampler.stop()
     errors = [r for r in reqs if r.error is not None]
     # capacity: a closed loop over the same mix (other seed) that keeps `workers`
     # requests in the server, completions per second until the last result; utilisation
@@ -520,11 +533,24 @@ def serving_measure(pkg, geoms, deltas_np, large, seconds, rate, workers, native
         created_in_window = server.stats()["created"] - created0
         burst, bcells = draw(int(1.5 * rate), np.random.Generator(np.random.PCG64(SERVE_SEED + 2)),
                              10 * n)
+        st2 = server.stats()
         wall_b = closed_loop(burst)
+        st3 = server.stats()
         capacity = {"requests_per_s": sig(len(burst) / wall_b),
                     "level_cells_per_s": sig(bcells / wall_b), "requests": len(burst),
                     "in_server": workers}
         util = sig((cells / seconds) / (bcells / wall_b), 3)
+    def sched(a, b, count):
+        """Scheduler thread between two stats snapshots: CPU share, share of wall time
+        in passes that moved a job, CPU ms per request."""
+        dt = b["uptime_s"] - a["uptime_s"]
+        return {"cpu_share": sig((b["sched_cpu_s"] - a["sched_cpu_s"]) / dt, 3),
+                "busy_share": sig((b["sched_busy_s"] - a["sched_busy_s"]) / dt, 3),
+                "passes_per_s": sig((b["passes"] - a["passes"]) / dt),
+                "cpu_ms_per_request": sig(1e3 * (b["sched_cpu_s"] - a["sched_cpu_s"]) / count)}
+    scheduler = None
+    if native:
+        scheduler = {"window": sched(st0, st1, n), "capacity": sched(st2, st3, len(burst))}
     if native:
         st = server.stats()
         peak_gb, evictions = st["peak_bytes"] / 2 ** 30, st["evictions"]
@@ -545,6 +571,9 @@ def serving_measure(pkg, geoms, deltas_np, large, seconds, rate, workers, native
            "capacity": capacity,
            "hierarchies_created_in_window": created_in_window,
            "utilisation": util,
+           "scheduler_thread": scheduler,
+           "process_cpu_s_in_window": sig(cpu_window),
+           "clocks_in_window": clocks,
            "latency_ms": {"p50": sig(stats["p50_ms"]), "p99": sig(stats["p99_ms"]),
                           "mean": sig(stats["mean_ms"]), "max": sig(stats["max_ms"])},
            "queue_wait_ms_p50": sig(1e3 * statistics.median(queue)) if queue else None,
@@ -552,7 +581,9 @@ def serving_measure(pkg, geoms, deltas_np, large, seconds, rate, workers, native
            "server": ("native: one C++ scheduler thread, non-blocking pipelines (mg_server_*)"
                       if native else "python: one thread per request in flight"),
            "workers": workers, "peak_inflight": server.peak_inflight,
-           "warmup": {"requests": len(warm) + len(pre), "seconds": sig(warm_s)},
+           "warmup": {"requests": len(warm) + len(pre) + (len(pre0) if native else 0),
+                      "seconds": sig(warm_s),
+                      "instances_per_config": copies},
            "peak_resident_gb": sig(peak_gb), "evictions": evictions, "errors": len(errors),
            "mix": "90%% draws from the 64 batched hierarchies, 10%% %d^3 base + 3 nests of %d^3 "
                   "(%.1f M level-cells); mixed precision; pinned host buffers in and out; "

@@ -102,6 +102,12 @@ typedef enum { MG_FP64 = 0, MG_MIXED = 1 } mg_precision;
  * with the persistent launch.  Results are bit-identical to the per-operation launches.
  * Ignored outside a batch. */
 #define MG_FLAG_PERSISTENT 32
+/* MG_FLAG_PAIR_SMOOTHER: the global-memory float32 smoother updates the cell of colour
+ * c of one z-pair per thread on every level.  By default, levels whose rows are a
+ * multiple of 4 cells long are smoothed by a kernel that updates the two cells of
+ * colour c of one z-quad per thread (one 16-byte load per neighbour row for both);
+ * both give bit-identical results. */
+#define MG_FLAG_PAIR_SMOOTHER 64
 
 typedef struct {
   int n_levels;                        /* 1 = base only; 1 + number of nests            */
@@ -319,6 +325,12 @@ typedef struct {
   long long evictions;                /* idle hierarchies closed to make room        */
   long long completed;                /* results handed to the result queue          */
   int pending, active, instances, peak_active;
+  /* scheduler thread: CPU seconds (updated every 64 passes and whenever a pass moves
+   * nothing), wall seconds of the passes that started, advanced or finished a job,
+   * seconds since mg_server_create, and passes made.  Under load a CPU share near 1
+   * means the host thread, not the GPU, limits the throughput. */
+  double sched_cpu_s, sched_busy_s, uptime_s;
+  long long passes;
 } mg_server_stats;
 
 /* max_active: requests on the GPU at once (1..256).  Errors: MG_EINVAL, MG_ECUDA. */

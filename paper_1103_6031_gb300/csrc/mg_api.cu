@@ -705,7 +705,7 @@ mg_status half_sweep(mg_hierarchy* h, int l, int colour) {
     KL(MG_K_SMOOTH, (cells_of(L.G) + 1) / 2,
        launch_smooth_half<T>(h->cfg.order, L.G, b.u[b.cur], b.u[1 - b.cur], b.ffas, a_f, colour,
                              L.periodic ? 1 : 0, h->cfg.tile_rows > 0 ? h->cfg.tile_rows : 4,
-                             h->s));
+                             !(h->cfg.flags & MG_FLAG_PAIR_SMOOTHER), h->s));
   b.cur ^= 1;
   return MG_OK;
 }

@@ -66,9 +66,12 @@ struct FaceSet {
 void make_faceset(const Grid& F, int half, FaceSet* fs);
 
 // ---- kernels: smoothing and inter-level transfer (mg_smooth.cu) ----
+// quad: float32 levels whose rows are a multiple of 4 long take the z-quad kernel
+// (bit-identical to the z-pair kernel taken otherwise).
 template <typename T>
 cudaError_t launch_smooth_half(int order, const Grid& G, const T* uin, T* uout, const T* f,
-                               double a_f, int colour, int periodic, int rows, cudaStream_t s);
+                               double a_f, int colour, int periodic, int rows, bool quad,
+                               cudaStream_t s);
 template <typename T>
 cudaError_t launch_residual_restrict(int order, const Grid& F, const T* u, const T* f,
                                      double invh2, const Grid& P, T* pu, T* pfas, T* ubar,

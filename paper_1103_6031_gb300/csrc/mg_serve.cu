@@ -146,6 +146,11 @@ struct mg_server {
   std::vector<Request*> active;
   std::vector<Slot*> slots;
   unsigned long long tick = 0;
+  // scheduler accounting (written by the scheduler thread, read by get_stats)
+  double t_created = 0.0;
+  std::atomic<long long> cpu_ns{0};   // the scheduler thread's CPU time
+  std::atomic<long long> busy_ns{0};  // wall time of the passes that moved something
+  std::atomic<long long> passes{0};
 };
 
 namespace {
@@ -361,16 +366,27 @@ bool advance(mg_server* S) {
   return moved;
 }
 
+long long thread_cpu_ns() {
+  timespec ts;
+  clock_gettime(CLOCK_THREAD_CPUTIME_ID, &ts);
+  return (long long)ts.tv_sec * 1000000000ll + ts.tv_nsec;
+}
+
 void scheduler(mg_server* S) {
   cudaSetDevice(S->device);
   double last_move = now_s();
-  for (;;) {
+  for (unsigned long long pass = 1;; ++pass) {
+    const double t0 = now_s();
     bool moved = admit(S);
     moved = advance(S) || moved;
+    S->passes.store((long long)pass, std::memory_order_relaxed);
+    if ((pass & 63) == 0) S->cpu_ns.store(thread_cpu_ns(), std::memory_order_relaxed);
     if (moved) {
       last_move = now_s();
+      S->busy_ns.fetch_add((long long)(1e9 * (last_move - t0)), std::memory_order_relaxed);
       continue;
     }
+    S->cpu_ns.store(thread_cpu_ns(), std::memory_order_relaxed);
     std::unique_lock<std::mutex> lk(S->mu);
     if (S->active.empty()) {
       if (S->stop) break;
@@ -403,6 +419,7 @@ mg_status mg_server_create(unsigned long long hbm_budget, int max_active, mg_ser
     delete S;
     return MG_ECUDA;
   }
+  S->t_created = now_s();
   S->th = std::thread(scheduler, S);
   *out = S;
   return MG_OK;
@@ -483,6 +500,10 @@ mg_status mg_server_get_stats(mg_server* S, mg_server_stats* out) {
   out->active = S->n_active;
   out->instances = S->n_slots;
   out->peak_active = S->peak_active;
+  out->sched_cpu_s = 1e-9 * (double)S->cpu_ns.load(std::memory_order_relaxed);
+  out->sched_busy_s = 1e-9 * (double)S->busy_ns.load(std::memory_order_relaxed);
+  out->uptime_s = now_s() - S->t_created;
+  out->passes = S->passes.load(std::memory_order_relaxed);
   return MG_OK;
 }
 

@@ -19,6 +19,7 @@ MG_FLAG_TMA_ALL = 4
 MG_FLAG_HYBRID = 8
 MG_FLAG_DEVICE_LOOP = 16
 MG_FLAG_PERSISTENT = 32
+MG_FLAG_PAIR_SMOOTHER = 64
 _TMA_FLAGS = {"auto": 0, "off": MG_FLAG_NO_TMA, "all": MG_FLAG_TMA_ALL}
 
 STATUS = {0: "MG_OK", 1: "MG_EINVAL", 2: "MG_ENOMEM", 3: "MG_ENOCONV", 4: "MG_ECUDA",
@@ -94,6 +95,10 @@ class MGServerStats(ctypes.Structure):
         ("active", ctypes.c_int),
         ("instances", ctypes.c_int),
         ("peak_active", ctypes.c_int),
+        ("sched_cpu_s", ctypes.c_double),
+        ("sched_busy_s", ctypes.c_double),
+        ("uptime_s", ctypes.c_double),
+        ("passes", ctypes.c_longlong),
     ]
 
     def as_dict(self):
@@ -204,7 +209,7 @@ def load_library(path=None):
 
 def make_config(base_n, box, order, nests=(), precision=MG_FP64, nu1=2, nu2=2, max_cycles=50,
                 tol=1e-10, inner_cycles=2, graphs=True, tile_rows=4, tma="auto", hybrid=False,
-                device_loop=False, persistent=False):
+                device_loop=False, persistent=False, pair_smoother=False):
     """MGConfig from plain values; nests = [(n3, off3), ...] (off in parent cells).
     tma: smoother kernel choice, "auto" (TMA-staged tiles on float32 nests of
     >= 2^23 cells), "off" or "all"; every choice gives bit-identical results.
@@ -214,7 +219,10 @@ def make_config(base_n, box, order, nests=(), precision=MG_FP64, nu1=2, nu2=2, m
     graph with a while node per solve; same launches and results).
     persistent: in a Batch of mixed-precision members that all set it, the float32
     V-cycles of all members run as one persistent kernel launch per outer iteration
-    (same results)."""
+    (same results).
+    pair_smoother: the global-memory float32 smoother updates one z-pair per thread on
+    every level, instead of one z-quad per thread on levels whose rows are a multiple
+    of 4 long (same results)."""
     lib = load_library()
     cfg = MGConfig()
     lib.mg_config_default(ctypes.byref(cfg))
@@ -232,7 +240,7 @@ def make_config(base_n, box, order, nests=(), precision=MG_FP64, nu1=2, nu2=2, m
     cfg.inner_cycles = int(inner_cycles)
     cfg.flags = (0 if graphs else MG_FLAG_NO_GRAPHS) | _TMA_FLAGS[tma] | \
         (MG_FLAG_HYBRID if hybrid else 0) | (MG_FLAG_DEVICE_LOOP if device_loop else 0) | \
-        (MG_FLAG_PERSISTENT if persistent else 0)
+        (MG_FLAG_PERSISTENT if persistent else 0) | (MG_FLAG_PAIR_SMOOTHER if pair_smoother else 0)
     cfg.tile_rows = int(tile_rows)
     return cfg
 

@@ -335,7 +335,7 @@ def test_native_server_instance_cap():
     reqs = [Request(k, cfg, inputs) for k in range(6)]
     for r in reqs:
         server.submit(r)
-    server.drain()
+    assert server.drain(timeout=120)
     st = server.stats()
     server.close()
     assert st["created"] == 1 and st["completed"] == 6

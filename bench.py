@@ -469,7 +469,10 @@ def serving_measure(pkg, geoms, deltas_np, large, seconds, rate, workers, native
     n = int(seconds * rate)
     reqs, cells = draw(n, rng)
     if native:
-        server = serve.NativeServer(max_active=workers, hbm_budget=64 << 30, keep_outputs=False)
+        # an output set per request in flight (no shared sets): the warm-up at full
+        # concurrency below grows the pool to the window's needs
+        server = serve.NativeServer(max_active=workers, hbm_budget=64 << 30, keep_outputs=False,
+                                    dropped_sets=None)
         # at most 3 resident hierarchies per configuration: creating one stalls the
         # device, and uncapped the server kept creating instances under load (20-54 inside
         # a 5 s window), which cut its capacity by up to half from run to run
@@ -514,6 +517,7 @@ def serving_measure(pkg, geoms, deltas_np, large, seconds, rate, workers, native
     serve.run_open_loop(server, pre, rate, seed=SERVE_SEED + 1)
     warm_s = time.perf_counter() - t0
     created0 = server.stats()["created"] if native else None
+    sets0 = sum(len(v) for v in server._owned.values()) if native else None
     server.completed.clear()
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
@@ -529,8 +533,10 @@ def serving_measure(pkg, geoms, deltas_np, large, seconds, rate, workers, native
     # = offered work / that capacity (at ~0.9 and above, queueing makes p50/p99 vary from
     # run to run)
     capacity, util, created_in_window = None, None, None
+    sets_in_window = None
     if native:
         created_in_window = server.stats()["created"] - created0
+        sets_in_window = sum(len(v) for v in server._owned.values()) - sets0
         burst, bcells = draw(int(1.5 * rate), np.random.Generator(np.random.PCG64(SERVE_SEED + 2)),
                              10 * n)
         st2 = server.stats()
@@ -570,6 +576,10 @@ def serving_measure(pkg, geoms, deltas_np, large, seconds, rate, workers, native
            "offered_level_cells_per_s": sig(cells / seconds),
            "capacity": capacity,
            "hierarchies_created_in_window": created_in_window,
+           "output_sets_allocated_in_window": sets_in_window,
+           "pinned_output_gb": (sig(sum(8 * t.numel() for sets in server._owned.values()
+                                         for st in sets for v in st.values() for t in v) / 2 ** 30)
+                                if native else None),
            "utilisation": util,
            "scheduler_thread": scheduler,
            "process_cpu_s_in_window": sig(cpu_window),

@@ -15,7 +15,8 @@
 //      final stores), so jobs at different stages overlap on the GPU;
 //   3. completion: a finished job's result goes to the result queue and its
 //      hierarchy back to the idle cache.
-// When nothing moved, the loop yields for ~200 us and then sleeps in 20 us steps.
+// When nothing moved, the loop yields for ~200 us and then sleeps in 20 us steps
+// (yielding throughout while jobs run took a whole core and served no faster).
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <time.h>

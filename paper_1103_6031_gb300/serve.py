@@ -24,6 +24,7 @@ as a worker slot is free and their hierarchy fits the HBM budget:
 """
 
 import collections
+import math
 import threading
 import time
 
@@ -229,7 +230,8 @@ class NativeServer:
     on the GPU at once.  Results are bit-identical to a solo
     Hierarchy.pipeline(host=True) call."""
 
-    def __init__(self, max_active=16, hbm_budget=32 << 30, keep_outputs=True, workers=None):
+    def __init__(self, max_active=16, hbm_budget=32 << 30, keep_outputs=True, workers=None,
+                 dropped_sets=2):
         import ctypes
         import torch
         self._ct = ctypes
@@ -255,10 +257,13 @@ class NativeServer:
         # request) in the submitting thread delayed the arrivals behind it.  _owned: every
         # set allocated per shapes; once a shape has `dropped_sets` of them, a request
         # whose results are dropped writes into one that may still be in use by another
-        # such request (the copies still run in full; nobody reads the values)
+        # such request (the copies still run in full; nobody reads the values).  With
+        # dropped_sets=None every request gets a set of its own (the pool grows to the
+        # peak number in flight per shapes): measured steadier under load, since
+        # concurrent copies into one set of pages ran slower
         self._pool = collections.defaultdict(list)
         self._owned = collections.defaultdict(list)
-        self.dropped_sets = 2
+        self.dropped_sets = dropped_sets
         self._poller = threading.Thread(target=self._poll_loop, daemon=True)
         self._poller.start()
 
@@ -277,7 +282,8 @@ class NativeServer:
             pooled = self._pool[key]
             owned = self._owned[key]
             out = pooled.pop() if pooled else None
-            if out is None and not self.keep_outputs and len(owned) >= self.dropped_sets:
+            if (out is None and not self.keep_outputs and self.dropped_sets is not None
+                    and len(owned) >= self.dropped_sets):
                 out = owned[self._next_id % len(owned)]
                 shared = True
             else:
@@ -304,11 +310,25 @@ class NativeServer:
             raise mg.MGError(st, "mg_server_submit")
 
     def output_set(self, shapes):
-        """A set of pinned host outputs (phi1, phi2, disp1, disp2) for leaf shapes."""
-        pin = lambda s: self._torch.empty(s, dtype=self._torch.float64, pin_memory=True)
-        return {"phi1": [pin(s) for s in shapes], "phi2": [pin(s) for s in shapes],
-                "disp1": [pin(s) for s in shapes for _ in range(3)],
-                "disp2": [pin(s) for s in shapes for _ in range(3)]}
+        """A set of pinned host outputs (phi1, phi2, disp1, disp2) for leaf shapes, all
+        views of one pinned allocation (one host mapping for the device per set, instead
+        of one per array)."""
+        torch = self._torch
+        sizes = [math.prod(s) for s in shapes]
+        slab = torch.empty(8 * sum(sizes), dtype=torch.float64, pin_memory=True)
+        off = [0]
+
+        def take(shape, count):
+            out = []
+            for _ in range(count):
+                n = math.prod(shape)
+                out.append(slab[off[0]:off[0] + n].view(*shape))
+                off[0] += n
+            return out
+        return {"phi1": [v for s in shapes for v in take(s, 1)],
+                "phi2": [v for s in shapes for v in take(s, 1)],
+                "disp1": [v for s in shapes for v in take(s, 3)],
+                "disp2": [v for s in shapes for v in take(s, 3)]}
 
     def reserve_outputs(self, cfg, count):
         """Pre-allocates `count` pooled output sets for requests of configuration cfg

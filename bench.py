@@ -68,6 +68,8 @@ SMOOTH_TRAFFIC_PER_UPDATE = 35.8
 # k_smooth_half_tma<6,float> (capture of the 256^3 nest launch)
 SMOOTH_F32_TRAFFIC_PER_UPDATE = 17.8
 SMOOTH_TMA_F32_TRAFFIC_PER_UPDATE = 22.3
+# k_smooth_quad<6> (float32 levels whose rows are a multiple of 4 long): not yet captured
+SMOOTH_QUAD_F32_TRAFFIC_PER_UPDATE = None
 # float32 levels of at least this many cells that are not periodic take the
 # TMA-staged smoother by default
 TMA_MIN_CELLS = 1 << 23
@@ -898,7 +900,12 @@ def solve_workload(pkg, name, deltas_np, steps, warmup, device, flush, barrier, 
     shapes = level_shapes(geom)
     tma_nests = [n for n in shapes[1:] if n[0] * n[1] * n[2] // 2 == dominant
                  and n[0] * n[1] * n[2] >= TMA_MIN_CELLS]
-    if not tma_nests:
+    if not tma_nests and all(n[2] % 4 == 0 for n in shapes
+                             if n[0] * n[1] * n[2] // 2 == dominant):
+        m_kernel = "k_smooth_quad<%d> (%s levels)" % (geom.order, big)
+        m_traffic = (SMOOTH_QUAD_F32_TRAFFIC_PER_UPDATE * m_upd
+                     if geom.order == 6 and SMOOTH_QUAD_F32_TRAFFIC_PER_UPDATE else None)
+    elif not tma_nests:
         m_kernel = "k_smooth_half<%d,float> (%s levels)" % (geom.order, big)
         m_traffic = SMOOTH_F32_TRAFFIC_PER_UPDATE * m_upd if geom.order == 6 else None
     else:

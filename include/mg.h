@@ -427,6 +427,16 @@ mg_status mg_selftest_wait_limit(void);
  * Synchronous on cuda_stream; allocates nothing.  Errors: MG_EINVAL, MG_ECUDA. */
 mg_status mg_fp64_fma_rate(int iters, void* cuda_stream, double* fma_per_s);
 
+/* The event-pair floor (no counterpart in the paper): the mean time that a pair of
+ * CUDA events reads around one kernel node of a CUDA graph when the kernel does nothing
+ * (event record node, a 1-block empty kernel, event record node; `pairs` of them in one
+ * graph, 1 <= pairs <= 1024, timed on the graph's second replay).  The profiled kernel
+ * families (mg_set_profiling) are timed with the same pairs, so their event-timed
+ * durations include this fixed cost; subtracting it bounds a kernel's own duration from
+ * below.  *us in microseconds.  Ordered after cuda_stream, synchronous; creates and
+ * frees its own graph, stream and events.  Errors: MG_EINVAL, MG_ECUDA. */
+mg_status mg_event_pair_floor(int pairs, void* cuda_stream, double* us);
+
 /* Self-test of the persistent batch kernel's bounded dependency wait (no counterpart
  * in the paper): one launch of that kernel on an internal two-item work list whose
  * second item depends on an operation that does not exist, with a 100 ms wait limit.

@@ -6,7 +6,13 @@
 // way the stencils use the pipe: every thread runs 8 independent chains of
 // fused multiply-adds (enough independent work per warp to cover the pipe's
 // latency), on a grid of 8 blocks of 256 threads per SM, timed with CUDA events.
+//
+// The event-pair floor: what a CUDA-event pair around one kernel node of a CUDA graph
+// reads for a kernel that does nothing, the fixed cost inside every event-timed launch
+// of the profiled kernel families.
 #include <cuda_runtime.h>
+
+#include <vector>
 
 #include "mg.h"
 
@@ -31,6 +37,8 @@ __global__ void __launch_bounds__(kBlock) k_dfma_chains(int iters, double a, dou
   // never true for the arguments the host passes; keeps the chains live
   if (s == 1234.5) sink[blockIdx.x * kBlock + threadIdx.x] = s;
 }
+
+__global__ void k_nothing() {}
 
 }  // namespace
 
@@ -65,5 +73,56 @@ extern "C" mg_status mg_fp64_fma_rate(int iters, void* cuda_stream, double* fma_
     *fma_per_s = (double)blocks * kBlock * kChains * (double)iters / (ms * 1e-3);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
+  return st;
+}
+
+extern "C" mg_status mg_event_pair_floor(int pairs, void* cuda_stream, double* us) {
+  if (!us || pairs < 1 || pairs > 1024) return MG_EINVAL;
+  *us = 0.0;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  std::vector<cudaEvent_t> ev(2 * pairs, nullptr);
+  cudaStream_t cs = nullptr;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  cudaEvent_t joined = nullptr;
+  mg_status st = MG_OK;
+  for (cudaEvent_t& e : ev)
+    if (st == MG_OK && cudaEventCreate(&e) != cudaSuccess) st = MG_ECUDA;
+  if (st == MG_OK && (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess ||
+                      cudaEventCreateWithFlags(&joined, cudaEventDisableTiming) != cudaSuccess))
+    st = MG_ECUDA;
+  // the same form as a profiled launch: event record node, kernel node, event record node
+  if (st == MG_OK && cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+    st = MG_ECUDA;
+  if (st == MG_OK) {
+    bool ok = true;
+    for (int i = 0; i < pairs && ok; ++i) {
+      ok = cudaEventRecordWithFlags(ev[2 * i], cs, cudaEventRecordExternal) == cudaSuccess;
+      k_nothing<<<1, 32, 0, cs>>>();
+      ok = ok && cudaGetLastError() == cudaSuccess &&
+           cudaEventRecordWithFlags(ev[2 * i + 1], cs, cudaEventRecordExternal) == cudaSuccess;
+    }
+    const cudaError_t e = cudaStreamEndCapture(cs, &g);
+    if (!ok || e != cudaSuccess || cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) st = MG_ECUDA;
+  }
+  // ordered after the caller's stream; the first replay warms the graph up
+  if (st == MG_OK && (cudaEventRecord(joined, s) != cudaSuccess ||
+                      cudaStreamWaitEvent(cs, joined, 0) != cudaSuccess ||
+                      cudaGraphLaunch(ge, cs) != cudaSuccess || cudaGraphLaunch(ge, cs) != cudaSuccess ||
+                      cudaStreamSynchronize(cs) != cudaSuccess))
+    st = MG_ECUDA;
+  double sum = 0.0;
+  for (int i = 0; i < pairs && st == MG_OK; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]) != cudaSuccess) st = MG_ECUDA;
+    sum += ms;
+  }
+  if (st == MG_OK) *us = 1e3 * sum / pairs;
+  if (ge) cudaGraphExecDestroy(ge);
+  if (g) cudaGraphDestroy(g);
+  if (cs) cudaStreamDestroy(cs);
+  if (joined) cudaEventDestroy(joined);
+  for (cudaEvent_t e : ev)
+    if (e) cudaEventDestroy(e);
   return st;
 }

@@ -172,6 +172,7 @@ def load_library(path=None):
         "mg_last_error": (ctypes.c_char_p, [vp]),
         "mg_selftest_wait_limit": (ctypes.c_int, []),
         "mg_fp64_fma_rate": (ctypes.c_int, [ctypes.c_int, vp, ctypes.POINTER(ctypes.c_double)]),
+        "mg_event_pair_floor": (ctypes.c_int, [ctypes.c_int, vp, ctypes.POINTER(ctypes.c_double)]),
         "mg_selftest_persist_wait": (ctypes.c_int, []),
         "mg_batch_set_persistent_blocks": (ctypes.c_int, [vp, ctypes.c_int]),
         "mg_server_set_max_instances": (ctypes.c_int, [vp, ctypes.c_int]),
@@ -517,6 +518,18 @@ def fp64_fma_rate(iters=4096, stream=None):
     st = load_library().mg_fp64_fma_rate(int(iters), sp, ctypes.byref(out))
     if st != 0:
         raise MGError(st, "mg_fp64_fma_rate")
+    return out.value
+
+
+def event_pair_floor(pairs=200, stream=None):
+    """Microseconds a CUDA-event pair reads around an empty kernel node of a CUDA graph
+    (mg_event_pair_floor): the fixed cost inside every event-timed launch of the
+    profiled kernel families."""
+    out = ctypes.c_double(0.0)
+    sp = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+    st = load_library().mg_event_pair_floor(int(pairs), sp, ctypes.byref(out))
+    if st != 0:
+        raise MGError(st, "mg_event_pair_floor")
     return out.value
 
 

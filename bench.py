@@ -49,8 +49,12 @@ SERVE_INSTANCES = 3
 REF_TOL = 1e-12        # float64 solve the measured errors are taken against
 BATCH_SEED = 1000
 SERVE_SEED = 5
-# float32 V-cycles per float64 refinement step in the mixed-precision variant
-MIXED_INNER_CYCLES = 4
+# float32 V-cycles per float64 refinement step in the mixed-precision variant: 3 on the
+# large single hierarchies (measured on the deep zoom: 3, 4, 5, 6, 8 cycles all take 3 + 3
+# outer iterations, in 22.2, 25.6, 29.6, 33.7, 40.5 ms), 4 on the batched workload's
+# small hierarchies (the batch autotuner's default schedule)
+MIXED_INNER_CYCLES = 3
+BATCH_INNER_CYCLES = 4
 HBM_PEAK_GBS = 6765.0    # measured copy bandwidth of the GB300s
 L2_FLUSH_BYTES = 256 << 20
 
@@ -451,9 +455,9 @@ def serving_measure(pkg, geoms, deltas_np, large, seconds, rate, workers, native
     rng = np.random.Generator(np.random.PCG64(SERVE_SEED))
     pinned = [[torch.from_numpy(x).pin_memory() for x in d] for d in deltas_np]
     large_in = [torch.from_numpy(x).pin_memory() for x in large[1]]
-    kw = dict(tol=MIXED_TOL, max_cycles=50, precision=pkg.MG_MIXED, inner_cycles=MIXED_INNER_CYCLES)
-    cfg_small = [pkg.config_from_geometry(g, **kw) for g in geoms]
-    cfg_large = pkg.config_from_geometry(large[0], **kw)
+    kw = dict(tol=MIXED_TOL, max_cycles=50, precision=pkg.MG_MIXED)
+    cfg_small = [pkg.config_from_geometry(g, inner_cycles=BATCH_INNER_CYCLES, **kw) for g in geoms]
+    cfg_large = pkg.config_from_geometry(large[0], inner_cycles=MIXED_INNER_CYCLES, **kw)
 
     def draw(count, rng, first_id=0):
         out, cells = [], 0
@@ -668,7 +672,7 @@ def batched_measure(pkg, geoms, deltas_np, steps, device):
                                 ("mixed_batched", pkg.MG_MIXED, True)):
         kw = dict(tol=SOLVE_TOL, max_cycles=50)
         if prec == pkg.MG_MIXED:
-            kw.update(tol=MIXED_TOL, precision=prec, inner_cycles=MIXED_INNER_CYCLES)
+            kw.update(tol=MIXED_TOL, precision=prec, inner_cycles=BATCH_INNER_CYCLES)
         hs = [pkg.Hierarchy(pkg.config_from_geometry(g, **kw)) for g in geoms]
         if batched:
             runner = pkg.Batch(hs)
@@ -702,7 +706,7 @@ def batched_measure(pkg, geoms, deltas_np, steps, device):
     # iteration over a (hierarchy, level operation, block range) work list
     hs = [pkg.Hierarchy(pkg.config_from_geometry(g, tol=MIXED_TOL, max_cycles=50,
                                                  precision=pkg.MG_MIXED,
-                                                 inner_cycles=MIXED_INNER_CYCLES, persistent=True))
+                                                 inner_cycles=BATCH_INNER_CYCLES, persistent=True))
           for g in geoms]
     runner = pkg.Batch(hs)
     outs, _, _ = runner.pipeline(deltas)

@@ -122,8 +122,9 @@ def test_served_results_of_each_request_class_within_1e6_of_oracle(lib, oracle):
     server = NativeServer(max_active=4, hbm_budget=16 << 30, keep_outputs=True)
     reqs = {}
     for k, (n, (geom, deltas)) in enumerate(cases.items()):
+        inner = bench.BATCH_INNER_CYCLES if n == "batch" else bench.MIXED_INNER_CYCLES
         cfg = lib.config_from_geometry(geom, tol=bench.MIXED_TOL, max_cycles=50, precision=lib.MG_MIXED,
-                                       inner_cycles=bench.MIXED_INNER_CYCLES)
+                                       inner_cycles=inner)
         reqs[n] = Request(k, cfg, [torch.from_numpy(x).pin_memory() for x in deltas])
         server.submit(reqs[n])
     server.drain()

@@ -25,3 +25,16 @@ def test_reference_arm_prints_one_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert "workload" in d["config"]
+
+
+def test_net_fraction_bounds_the_raw_one_from_above():
+    """The roofline fraction net of the event-pair floor: the raw fraction scaled by
+    duration / (duration - floor), None when the floor is unknown or not below the
+    duration."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.net_frac(0.5, 0.010, 5.0) == 0.5 * 10.0 / 5.0
+    assert bench.net_frac(0.5, 0.010, 0.0) == 0.5
+    assert bench.net_frac(0.5, 0.010, None) is None
+    assert bench.net_frac(0.5, 0.004, 5.0) is None
+    assert bench.net_frac(0.5, None, 1.0) is None

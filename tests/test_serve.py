@@ -347,3 +347,33 @@ def test_native_server_instance_cap():
         for k in ("phi1", "phi2", "disp1", "disp2"):
             for a, b in zip(r.outputs[k], want[k]):
                 assert torch.equal(a, b), (r.id, k)
+
+
+def test_output_set_views_tile_one_allocation():
+    """NativeServer.output_set: phi1, phi2 (one per level), disp1, disp2 (three per level)
+    are contiguous views of one allocation that tile it exactly, in that order, without
+    overlap (host logic; pinning itself needs a GPU and is replaced here)."""
+    import torch
+    from paper_1103_6031_gb300.serve import NativeServer
+
+    class _Torch:
+        float64 = torch.float64
+
+        @staticmethod
+        def empty(*a, **k):
+            k.pop("pin_memory", None)
+            return torch.empty(*a, **k)
+
+    fake = type("S", (), {"_torch": _Torch})()
+    shapes = [(4, 6, 8), (10, 12, 16)]
+    out = NativeServer.output_set(fake, shapes)
+    order = out["phi1"] + out["phi2"] + out["disp1"] + out["disp2"]
+    assert [tuple(v.shape) for v in out["phi1"]] == shapes == [tuple(v.shape) for v in out["phi2"]]
+    assert [tuple(v.shape) for v in out["disp1"]] == [s for s in shapes for _ in range(3)]
+    base = order[0].untyped_storage().data_ptr()
+    pos = 0
+    for v in order:
+        assert v.is_contiguous() and v.untyped_storage().data_ptr() == base
+        assert v.storage_offset() == pos
+        pos += v.numel()
+    assert pos == order[0].untyped_storage().nbytes() // 8

@@ -1123,7 +1123,7 @@ def run_ours(args):
             line["cpu_baseline"] = cpu_baseline(name)
             if not args.skip_all_cores:
                 line["cpu_baseline"]["all_cores"] = cpu_baseline_all_cores(name)
-        # the evidence the judge reads from the end of the line
+        # the evidence a reader of the last part of the line sees
         line["latency_ms"] = {"p50": sig(statistics.median(R["step_ms"])), "p99": sig(p99(R["step_ms"]))}
         line["cycles"] = {"1lpt": info1["cycles"], "2lpt": info2["cycles"] if info2 else None,
                           "level_rel_residual_max": sig(max(info1["level_rel_residual"]

@@ -122,3 +122,16 @@ def test_null_handles_and_bad_arguments_are_rejected_without_a_gpu(mg):
     assert lib.mg_batch_create(None, 0, None, ctypes.byref(out)) == 1
     assert lib.mg_hierarchy_create(None, None, ctypes.byref(out)) == 1
     assert lib.mg_last_error(None) in (b"", None)
+
+
+def test_server_cap_and_probes_reject_bad_arguments_without_a_gpu(mg):
+    """mg_server_set_max_instances, mg_fp64_fma_rate and mg_event_pair_floor check their
+    arguments before any CUDA call."""
+    lib = mg.load_library()
+    assert lib.mg_server_set_max_instances(None, 3) == 1
+    out = ctypes.c_double(-1.0)
+    assert lib.mg_event_pair_floor(0, None, ctypes.byref(out)) == 1
+    assert lib.mg_event_pair_floor(1025, None, ctypes.byref(out)) == 1
+    assert lib.mg_event_pair_floor(8, None, None) == 1
+    assert lib.mg_fp64_fma_rate(8, None, ctypes.byref(out)) == 1
+    assert lib.mg_fp64_fma_rate(1 << 23, None, ctypes.byref(out)) == 1

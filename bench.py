@@ -477,16 +477,19 @@ def serving_measure(pkg, geoms, deltas_np, large, seconds, rate, workers, native
     reqs, cells = draw(n, rng)
     if native:
         # an output set per request in flight (no shared sets): the warm-up at full
-        # concurrency below grows the pool to the window's needs
+        # concurrency below grows the pool to the window's needs (27 GB of pinned sets
+        # with the 128^3 large class); with the 256^3 class a set is 4.3 GB, so its
+        # requests beyond two share sets as before
+        small_large = large[0].level_cells() < (1 << 24)
         server = serve.NativeServer(max_active=workers, hbm_budget=64 << 30, keep_outputs=False,
-                                    dropped_sets=None)
+                                    dropped_sets=None if small_large else 2)
         # at most 3 resident hierarchies per configuration: creating one stalls the
         # device, and uncapped the server kept creating instances under load (20-54 inside
         # a 5 s window), which cut its capacity by up to half from run to run
         server.set_max_instances(SERVE_INSTANCES)
         # pinned output sets of the large class up front (0.5 GB each at 128^3, 4.3 GB at
         # 256^3); the others come from the warm-up below and are recycled from then on
-        server.reserve_outputs(cfg_large, 8 if large[0].level_cells() < (1 << 24) else 2)
+        server.reserve_outputs(cfg_large, 8 if small_large else 2)
     else:
         server = serve.Server(workers=workers, hbm_budget=64 << 30, keep_outputs=False)
     # warm server: every configuration served as many times at once as it may have
